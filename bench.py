@@ -1,0 +1,363 @@
+"""Benchmark of the NDG + RK hot path on B300: DOF-updates per second per RK stage.
+
+Workload (one bench step): the 2D linear advection problem of the paper's Sec. 3 at degree 7,
+256 x 256 quadrilateral elements (8 x 8 LGL nodes each, 2048^2 = 4.19M DOF), velocity (1, 0.5),
+Gaussian pulse exp(-r^2/0.01) at the centre plus seeded low-mode Fourier noise (amplitude 1e-3),
+upwind flux, classical RK4 at CFL 0.1, 1000 time steps, followed by the norms reduction.  The
+state is reset from a device-resident copy of the initial condition and L2 is flushed at the start
+of every bench step.  FP64 is the headline; the FP32 variant and a mixed serving stream are
+reported beside it; the FP64 CPU oracle (single thread, as it stands) gives the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-serving]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload ("replicas only":
+the solve is not partitioned across GPUs); value = total DOF-updates / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s per RK stage (FP64 vs FP32); batched solves/s + p50/p99 latency"
+DIM, DEGREE, ELEMS, VEL, CFL, NSTEPS, RK = 2, 7, (256, 256), (1.0, 0.5, 0.0), 0.1, 1000, 4
+STAGES = 4
+WORKLOAD = "2D linear advection, 256x256 elements, degree 7 (8x8 LGL nodes), 4.19M DOF, RK4, 1000 steps"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic work of one RK4 stage per DOF for 2D advection at degree 7:
+#   flops: sum-factorised strong-form volume term 2 axes x 8 FMA (32 flop) + per-axis scaling (3)
+#          + lifted face terms (1.5) + stage update (3.5 on average over the 4 stages) = 40 flop;
+#   bytes: RK4 array passes per stage 3, 5, 5, 3 -> 4 on average x sizeof(real).
+FLOPS_PER_DOF_STAGE = 40.0
+PASSES_PER_STAGE = 4.0
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def fp64_peak_tflops(sm_mhz):
+    # 148 SMs x 2 DFMA / clock / SM x 2 flop (B300 FP64 units; 1.12 TFLOP/s measured at 1935 MHz)
+    return 148 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+                self.lines = [l for l in out.splitlines() if l.strip()]
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, dev=None):
+    if pg is not None:
+        if dev is not None:
+            pg.barrier(device_ids=[dev])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, x, dev):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{dev}" if dev is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def initial_condition(X):
+    from paper_2510_05254_b300 import inputs
+    return inputs.gaussian_noise(X)
+
+
+def oracle_sample(nsteps):
+    """The FP64 oracle as it stands (single thread) on the full workload for nsteps RK4 steps."""
+    from oracle import oracle as orc
+    p = orc.Problem(dim=DIM, degree=DEGREE, elems=ELEMS + (1,), equation=0, flux=0, velocity=VEL)
+    U0 = initial_condition(orc.node_coords(p))
+    dt = orc.stable_dt(p, U0, CFL)
+    t = time.perf_counter()
+    orc.step(p, U0, dt, nsteps, RK)
+    el = time.perf_counter() - t
+    return p.ndof * STAGES * nsteps / el, el
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    sample_steps = 1
+    for _ in range(args.warmup):
+        oracle_sample(sample_steps)
+    rates, tot = [], 0.0
+    for _ in range(args.steps):
+        r, el = oracle_sample(sample_steps)
+        rates.append(r)
+        tot += el
+    value = statistics.median(rates)
+    sample = f"{sample_steps} RK4 step of the full 4.19M-DOF workload per bench step (1000 in the GPU step)"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(world),
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def config_block(world):
+    return {"workload": WORKLOAD, "model": "NDG+RK4 2D linear advection (degree 7)", "global_batch": world,
+            "seq_len": None, "elements": list(ELEMS), "degree": DEGREE, "dof": 256 * 256 * 64,
+            "rk_steps_per_bench_step": NSTEPS, "parallelism": f"replicas{world}",
+            "l2": f"flushed at the start of every bench step ({L2_FLUSH_BYTES >> 20} MiB write, inside the timed region)"}
+
+
+def run_solver_timed(dtype, args, dev, pg, U0_host):
+    """Device-timed bench steps of one dtype: returns per-step device ms and stage-kernel ms."""
+    import torch
+    from paper_2510_05254_b300.solver import Solver
+    s = Solver(DIM, DEGREE, ELEMS, velocity=VEL, dtype=dtype, device=dev)
+    U0 = torch.tensor(U0_host, device=f"cuda:{dev}", dtype=s.torch_dtype)
+    s.set_state(U0)
+    dt = s.stable_dt(CFL)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    from paper_2510_05254_b300 import native as nat
+
+    def one(evs=None):
+        with torch.cuda.stream(s.stream):
+            flush.zero_()
+        nat.ndg_set_state(s.ctx, U0.data_ptr(), s.state_bytes, True)
+        if evs:
+            evs[0].record(s.stream)
+        nat.ndg_step(s.ctx, dt, NSTEPS, RK)
+        if evs:
+            evs[1].record(s.stream)
+        return nat.ndg_norms(s.ctx)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize(dev)
+    barrier(pg, dev)
+    torch.cuda.synchronize(dev)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    inner = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(dev) as clk:
+        start.record(s.stream)
+        for k in range(args.steps):
+            nr = one(inner[k])
+        end.record(s.stream)
+        torch.cuda.synchronize(dev)
+    barrier(pg, dev)
+    total_ms = start.elapsed_time(end)
+    stage_ms = sum(a.elapsed_time(b) for a, b in inner) / (args.steps * NSTEPS * STAGES)
+    out = {"total_ms": total_ms, "stage_ms": stage_ms, "ndof": s.ndof, "dt": dt, "clocks": clk.summary(),
+           "l2_norm": nr.l2, "mass": nr.integral[0], "state_bytes": s.state_bytes}
+    s.close()
+    return out
+
+
+def run_e2e(args, dev, U0_host):
+    """Same workload through the C ABI with HOST buffers: pinned H2D of the initial state, 1000 RK
+    steps, D2H of the final state and of the norms, every bench step."""
+    import torch
+    from paper_2510_05254_b300 import native as nat
+    from paper_2510_05254_b300.solver import Solver
+    s = Solver(DIM, DEGREE, ELEMS, velocity=VEL, dtype="f64", device=dev)
+    src = torch.tensor(U0_host, dtype=torch.float64).pin_memory()
+    dst = torch.empty_like(src).pin_memory()
+    s.set_state(U0_host)
+    dt = s.stable_dt(CFL)
+
+    def one():
+        nat.ndg_set_state(s.ctx, src.data_ptr(), s.state_bytes, False)
+        nat.ndg_step(s.ctx, dt, NSTEPS, RK)
+        nat.ndg_get_state(s.ctx, dst.data_ptr(), s.state_bytes, False)
+        return nat.ndg_norms(s.ctx)
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t
+    nb = s.state_bytes
+    s.close()
+    return el, nb
+
+
+def run_serving(args, dev):
+    from paper_2510_05254_b300 import inputs, serving
+    n = args.serving_solves
+    reqs = serving.prepare(inputs.serving_stream(n, emax=args.serving_emax), nsteps=100)
+    import torch
+    budget = 120 << 30
+    pool_stats, _ = serving.run_pool(reqs, math.inf, budget)
+    torch.cuda.synchronize(dev)
+    serial_stats, _ = serving.run_serial(reqs, math.inf)
+    # latency at a finite arrival rate: half of the pool's measured capacity
+    rate = 0.5 * pool_stats["solves_per_s"]
+    pool_rate_stats, _ = serving.run_pool(reqs, rate, budget)
+    return {"workload": f"{n} independent 2D solves (advection / isothermal Euler 50/50, elements per axis "
+                        f"log-uniform in [16,{args.serving_emax}], degree in {{3,5,7}}, FP64/FP32 50/50), "
+                        "100 RK4 steps each, 120 GB budget",
+            "burst": {"pool": pool_stats, "one_at_a_time": serial_stats,
+                      "speedup_solves_per_s": pool_stats["solves_per_s"] / serial_stats["solves_per_s"]},
+            "poisson_half_capacity": {"rate_per_s": rate, "pool": pool_rate_stats}}
+
+
+def run_ours(args, world, rank, dev, pg):
+    import torch
+    from paper_2510_05254_b300.solver import Solver
+    peaks, peak_kind = load_peaks()
+    probe = Solver(DIM, DEGREE, ELEMS, velocity=VEL, dtype="f64", device=dev)
+    X = probe.node_coords()
+    probe.close()
+    U0 = np.ascontiguousarray(initial_condition(X))
+    r64 = run_solver_timed("f64", args, dev, pg, U0)
+    r32 = run_solver_timed("f32", args, dev, pg, U0)
+    t64 = max_over_ranks(pg, r64["total_ms"], dev)
+    t32 = max_over_ranks(pg, r32["total_ms"], dev)
+    work = r64["ndof"] * STAGES * NSTEPS * args.steps
+    value = world * work / (t64 * 1e-3)
+    value32 = world * work / (t32 * 1e-3)
+    e2e_s, nb = run_e2e(args, dev, U0)
+    e2e_s = max_over_ranks(pg, e2e_s, dev)
+    # roofline of the dominant kernel (the fused stage kernel)
+    clocks = r64["clocks"] or {}
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    p64 = fp64_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+    ach64 = FLOPS_PER_DOF_STAGE * r64["ndof"] / (r64["stage_ms"] * 1e-3) / 1e12
+    bytes32 = PASSES_PER_STAGE * 4 * r32["ndof"]
+    ach32 = bytes32 / (r32["stage_ms"] * 1e-3) / 1e9
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian pulse + Fourier noise)",
+        "config": config_block(world),
+        "e2e": {"value": world * work / e2e_s, "unit": "DOF-updates/s", "h2d_bytes_per_step": nb,
+                "d2h_bytes_per_step": nb + 8 * 8},
+        "gpu_launches": args.steps * (NSTEPS * STAGES + 2),
+        "roofline": {"bound": "alu", "achieved": ach64, "peak": p64, "unit": "TFLOP/s", "frac": ach64 / p64,
+                     "traffic": None, "kernel": "stage_kernel<2,7,adv,double>",
+                     "peak_note": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop at the max SM clock (derived)",
+                     "stage_ms": r64["stage_ms"]},
+        "f32": {"value": value32, "unit": "DOF-updates/s", "ms_per_step": t32 / args.steps,
+                "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
+                             "frac": ach32 / hbm, "traffic": None, "kernel": "stage_kernel<2,7,adv,float>",
+                             "peak_kind": peak_kind, "stage_ms": r32["stage_ms"],
+                             "note": "working set 4 x 16.8 MB fits the 126 MB L2: stages after the first read L2"}},
+        "clocks": r64["clocks"],
+        "check": {"l2_norm_f64": r64["l2_norm"], "l2_norm_f32": r32["l2_norm"], "mass_f64": r64["mass"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, el = oracle_sample(args.cpu_steps)
+        line["cpu_baseline"] = {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{args.cpu_steps} RK4 steps of the full 4.19M-DOF workload "
+                                          f"({el:.1f} s, single-threaded FP64 oracle)"}
+    if rank == 0 and not args.no_serving:
+        line["serving"] = run_serving(args, dev)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=15)
+    ap.add_argument("--serving-solves", type=int, default=200)
+    ap.add_argument("--serving-emax", type=int, default=512)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_ours(args, world, rank, local, pg)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,51 @@
+// Host-side helpers of libndg shared by the C-ABI implementation (api.cu) and the serving pool
+// (pool.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/ndg.h"
+#include "ndg_internal.h"
+
+namespace ndg {
+
+// error reporting (thread-local message for ndg_last_error)
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+// device memory through the optional allocator hook
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream);
+void dev_free(void* p, cudaStream_t stream);
+
+const std::vector<StagePlan>& stage_plans(int rk);
+int num_roles_for(int rk);
+bool valid_rk(int rk);
+
+// Launch resources of one kernel class over a set of solves (one persistent launch per stage).
+struct Group {
+  KernelClass kc{};
+  int epb = 0;
+  int grid = 0;
+  int ntiles = 0;
+  std::vector<SolveDesc> h_desc;
+  SolveDesc* d_desc = nullptr;
+  GroupHeader* d_hdr = nullptr;
+  size_t cap = 0;
+};
+int group_upload(Group& g, cudaStream_t stream);
+void group_free(Group& g, cudaStream_t stream);
+// Capture one RK step of scheme rk (all stages) of the groups, as parallel branches.
+int capture_step(const std::vector<Group*>& groups, int rk, cudaStream_t cap, cudaGraphExec_t* out);
+
+int num_sms(int device);
+int default_epb(const KernelClass& kc);
+int tuned_epb(const KernelClass& kc);
+
+// Geometry part of a solve descriptor (scales, lift coefficients, element counts).
+void fill_solve_geometry(const ndg_config& cfg, const Basis& b, SolveDesc* d);
+// Validate a configuration (no device access); NDG_OK or NDG_EINVAL with a message.
+int check_config(const ndg_config& k);
+
+}  // namespace ndg

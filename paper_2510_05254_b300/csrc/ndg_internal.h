@@ -1,0 +1,102 @@
+// Internal declarations shared by the host code and the CUDA kernels of libndg.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace ndg {
+
+constexpr int kMaxDegree = 7;
+constexpr int kMaxN = kMaxDegree + 1;
+constexpr int kMaxStages = 7;
+
+// FP64 LGL basis of one degree (host-built, then uploaded).
+struct Basis {
+  int degree;
+  double xi[kMaxN];
+  double w[kMaxN];
+  double D[kMaxN * kMaxN];   // D[i*n + m] = h_m'(xi_i), row-major with stride n = degree + 1
+  double Ae[kMaxN * kMaxN];  // even-odd halves, stride kMaxN (see build_basis)
+  double Bo[kMaxN * kMaxN];
+  double Cmid[kMaxN];        // D[i][mid] for odd n
+  double Dmid[kMaxN];        // D[mid][m] for odd n
+};
+
+bool build_basis(int N, Basis* b);
+
+// Buffer roles of one solve.  UN: the state U^n; ACC: the running sum U^n + dt sum_j b_j k_j;
+// S0/S1: ping-pong stage inputs; K0..K6: stored stage slopes (RK6 only).
+enum BufRole { kUN = 0, kACC = 1, kS0 = 2, kS1 = 3, kK0 = 4, kNumRoles = 11 };
+
+// What one RK stage reads and writes, common to every solve of a launch (from the tableau).
+// With L = L(U_in) the stage's right-hand side:
+//   u_out = base + sum_j a_read[j] * dt * K[kread[j]] + a_self * dt * L   (base = UN)
+//   acc_mode 1: ACC = base + b*dt*L; 2: ACC += b*dt*L; 3 (last stage): u_out = ACC + b*dt*L;
+//   0: ACC untouched.  kwrite >= 0 stores L into that role (the slopes K hold L, not dt*L).
+struct StagePlan {
+  int in;         // role of the stage input (the tile is read from it, with neighbour traces)
+  int out;        // role written with the next stage input (or U^{n+1} at the last stage)
+  int kwrite;     // role to store L in, or -1
+  int nread;      // number of stored slopes in the stage combination
+  int kread[kMaxStages];
+  double a_read[kMaxStages];
+  double a_self;
+  int acc_mode;
+  double b;
+};
+
+// One solve inside a launch (device memory; read by every CTA working on it).
+struct SolveDesc {
+  void* buf[kNumRoles];   // device pointers by role (dtype of the launch class)
+  int E[3];               // elements per axis (1 beyond dim)
+  int tile_begin;         // first global tile index of this solve in the launch
+  long long nelem;
+  double vol_scale[3];    // -2/h_a (Euler) or -2 a_a / h_a (advection): multiplies D F
+  double lift_lo[3];      // advection: (2/h_a)(1/w_0) (a_a + |a_a|)/2; Euler: (1/h_a)/w_0
+  double lift_hi[3];      // advection: (2/h_a)(1/w_N) (a_a - |a_a|)/2; Euler: (1/h_a)/w_N
+  double c2;              // c^2 (Euler)
+  double c;               // c (Euler, LLF alpha)
+  double dt;
+};
+
+// Header of a launch's work list (device memory): tiles are numbered across all solves.
+struct GroupHeader {
+  int nsolves;
+  int ntiles;
+  int epb;                // elements per CTA tile
+  int pad;
+};
+
+// Kernel class: everything that is a template parameter of the stage kernel.
+struct KernelClass {
+  int dim, degree, equation, dtype;
+  bool operator==(const KernelClass& o) const {
+    return dim == o.dim && degree == o.degree && equation == o.equation && dtype == o.dtype;
+  }
+};
+
+// Launch one RK stage of the fused kernel for a group: `grid` CTAs loop over the group's tiles.
+// Returns a cudaError_t value.
+int launch_stage(const KernelClass& kc, int grid, int epb, const SolveDesc* solves,
+                 const GroupHeader* header, const StagePlan& plan, void* stream);
+// Threads and dynamic shared memory of one CTA for a class and tile size.
+void stage_launch_shape(const KernelClass& kc, int epb, int* threads, size_t* smem_bytes);
+// Ensure the kernel's attributes (max dynamic smem) are set; returns cudaError_t.
+int prepare_stage_kernel(const KernelClass& kc, int epb, int* max_blocks_per_sm);
+
+// Upload the basis of every degree to constant memory on the current device (idempotent).
+int upload_bases();
+
+// Norm reduction: partial sums per block into `partials` (nblocks * kNormFields doubles), then
+// the final single-block pass into `result` (kNormFields doubles).
+constexpr int kNormFields = 10;  // l2sq, linf, integral[4], max_speed, nonfinite, spare x2
+int launch_norms(int dtype, int dim, int degree, int equation, const void* U, const void* ref,
+                 long long nelem, double jac, double c, const double* velocity, int nblocks,
+                 double* partials, double* result, void* stream);
+constexpr int kNormBlocks = 296;
+
+// Layout conversion between element layout and grid layout (device to device).
+int launch_relayout(int dtype, int dim, int degree, int nvar, const int* E, const void* src,
+                    void* dst, bool to_element, void* stream);
+
+}  // namespace ndg

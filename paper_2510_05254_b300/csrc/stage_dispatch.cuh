@@ -1,0 +1,95 @@
+// Instantiation of the fused stage kernel for one (precision, dimension) pair, degrees 1..7 and
+// both equations.  Each stage_<dtype>_d<dim>.cu includes this with NDG_REAL / NDG_DIM defined.
+#include <cstring>
+#include <mutex>
+
+#include "stage_kernel.cuh"
+
+namespace ndg {
+
+namespace {
+
+template <typename real>
+const BasisArgs<real>& basis_args(int N) {
+  static BasisArgs<real> table[kMaxDegree + 1];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int d = 1; d <= kMaxDegree; ++d) {
+      Basis b;
+      build_basis(d, &b);
+      BasisArgs<real>& t = table[d];
+      std::memset(&t, 0, sizeof(t));
+      const int n = d + 1, h = n / 2;
+      for (int i = 0; i < h; ++i)
+        for (int m = 0; m < h; ++m) {
+          t.Ae[i * 4 + m] = (real)b.Ae[i * kMaxN + m];
+          t.Bo[i * 4 + m] = (real)b.Bo[i * kMaxN + m];
+        }
+      for (int i = 0; i < h; ++i) {
+        t.Cmid[i] = (real)b.Cmid[i];
+        t.Dmid[i] = (real)b.Dmid[i];
+      }
+    }
+  });
+  return table[N];
+}
+
+template <int N, int EQ>
+int launch_one(int grid, int epb, const SolveDesc* solves, const GroupHeader* header,
+               const StagePlan& plan, void* stream) {
+  StageArgs<NDG_REAL> args;
+  args.solves = solves;
+  args.hdr = header;
+  args.plan = plan;
+  args.basis = basis_args<NDG_REAL>(N);
+  int threads;
+  size_t smem;
+  stage_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, &threads, &smem);
+  stage_kernel<NDG_DIM, N, EQ, NDG_REAL><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
+  return (int)cudaGetLastError();
+}
+
+template <int N, int EQ>
+int prepare_one(int epb, int* max_blocks) {
+  int threads;
+  size_t smem;
+  stage_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, &threads, &smem);
+  auto fn = stage_kernel<NDG_DIM, N, EQ, NDG_REAL>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  int nb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
+  if (max_blocks) *max_blocks = nb;
+  return (int)e;
+}
+
+template <int N, int EQ>
+void shape_one(int epb, int* threads, size_t* smem) {
+  stage_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, threads, smem);
+}
+
+}  // namespace
+
+#define NDG_CAT2(a, b) a##b
+#define NDG_CAT(a, b) NDG_CAT2(a, b)
+#define NDG_SWITCH(CALL)                                         \
+  switch (degree * 2 + equation) {                               \
+    case 2: return CALL<1, 0>; case 3: return CALL<1, 1>;        \
+    case 4: return CALL<2, 0>; case 5: return CALL<2, 1>;        \
+    case 6: return CALL<3, 0>; case 7: return CALL<3, 1>;        \
+    case 8: return CALL<4, 0>; case 9: return CALL<4, 1>;        \
+    case 10: return CALL<5, 0>; case 11: return CALL<5, 1>;      \
+    case 12: return CALL<6, 0>; case 13: return CALL<6, 1>;      \
+    case 14: return CALL<7, 0>; case 15: return CALL<7, 1>;      \
+    default: break;                                              \
+  }
+
+using LaunchFn = int (*)(int, int, const SolveDesc*, const GroupHeader*, const StagePlan&, void*);
+using PrepareFn = int (*)(int, int*);
+using ShapeFn = void (*)(int, int*, size_t*);
+
+LaunchFn NDG_CAT(NDG_TAG, _launch)(int degree, int equation) { NDG_SWITCH(&launch_one) return nullptr; }
+PrepareFn NDG_CAT(NDG_TAG, _prepare)(int degree, int equation) { NDG_SWITCH(&prepare_one) return nullptr; }
+ShapeFn NDG_CAT(NDG_TAG, _shape)(int degree, int equation) { NDG_SWITCH(&shape_one) return nullptr; }
+
+}  // namespace ndg

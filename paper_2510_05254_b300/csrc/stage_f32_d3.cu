@@ -1,0 +1,5 @@
+// Fused stage kernels, float, 3D, degrees 1..7, both equations.
+#define NDG_REAL float
+#define NDG_DIM 3
+#define NDG_TAG stage_f32_d3
+#include "stage_dispatch.cuh"

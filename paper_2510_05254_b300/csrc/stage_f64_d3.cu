@@ -1,0 +1,5 @@
+// Fused stage kernels, double, 3D, degrees 1..7, both equations.
+#define NDG_REAL double
+#define NDG_DIM 3
+#define NDG_TAG stage_f64_d3
+#include "stage_dispatch.cuh"

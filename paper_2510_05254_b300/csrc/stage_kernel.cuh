@@ -1,0 +1,325 @@
+// Fused NDG right-hand side + Runge-Kutta stage update (one launch per RK stage).
+//
+// Method (arXiv:2510.05254, Sec. 2.1-2.3), strong form of the collocated LGL scheme: along every
+// axis a of a tensor-product element, for every line of n = N+1 nodes,
+//   dU_l/dt += -(2/h_a) (D F_a)_l
+//              + (2/h_a)/w_0 (Fhat_lo - F_a(U_0)) delta_{l0}
+//              + (2/h_a)/w_N (F_a(U_N) - Fhat_hi) delta_{lN},
+// which equals the paper's weak form (volume integral by LGL quadrature, lumped mass of
+// Eq. (lag_coefs)) through the summation-by-parts identity W D + D^T W = diag(-1, 0.., 1).
+// Fhat is the Lax-Friedrichs flux of Eq. (LF): for advection the upwind flux, for isothermal
+// Euler alpha = max(|u_a^-|, |u_a^+|) + c.  The stage update applies the Butcher tableau of
+// Eq. (RK3)/(RK4)/(RK6) as described by StagePlan.
+//
+// Work decomposition: a CTA owns a tile of `epb` consecutive elements (in the element layout a
+// contiguous chunk of every variable).  Phases, separated by __syncthreads:
+//   1. copy the tile of the stage input into shared memory (x-lines padded by one slot);
+//   2. Euler: velocities u_a = m_a / rho per node into shared memory;
+//   3. for each axis a: one thread per line of n nodes evaluates the flux along the line,
+//      applies D by its even-odd halves (D is centro-antisymmetric on LGL nodes), adds the
+//      lifted face terms at the two ends (neighbour traces from shared memory when the
+//      neighbour element is in the tile, else from global memory / L2), and accumulates into
+//      the shared right-hand side;
+//   4. node-parallel stage update with coalesced global reads/writes.
+// The grid is persistent: CTAs loop over the tiles of every solve of the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ndg_internal.h"
+
+namespace ndg {
+
+constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
+
+// Basis of one degree in the launch's precision, passed by value (lives in the kernel's
+// constant bank, so the contraction's coefficients are constant operands).
+template <typename real>
+struct BasisArgs {
+  real Ae[16];   // [i*4 + m], i, m < n/2
+  real Bo[16];
+  real Cmid[4];  // D[i][mid], odd n
+  real Dmid[4];  // D[mid][m], odd n
+};
+
+template <typename real>
+struct StageArgs {
+  const SolveDesc* solves;
+  const GroupHeader* hdr;
+  StagePlan plan;
+  BasisArgs<real> basis;
+};
+
+template <int N, typename real>
+__device__ __forceinline__ void contract_even_odd(const real (&f)[N + 1], real (&out)[N + 1],
+                                                  const BasisArgs<real>& B) {
+  constexpr int n = N + 1;
+  constexpr int H = n / 2;
+  real fe[H], fo[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    fe[m] = f[m] + f[N - m];
+    fo[m] = f[m] - f[N - m];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    real E = B.Ae[i * 4] * fo[0];
+    real O = B.Bo[i * 4] * fe[0];
+#pragma unroll
+    for (int m = 1; m < H; ++m) {
+      E = fma(B.Ae[i * 4 + m], fo[m], E);
+      O = fma(B.Bo[i * 4 + m], fe[m], O);
+    }
+    if (n % 2 == 1) O = fma(B.Cmid[i], f[H], O);
+    out[i] = E + O;
+    out[N - i] = E - O;
+  }
+  if (n % 2 == 1) {
+    real M = B.Dmid[0] * fo[0];
+#pragma unroll
+    for (int m = 1; m < H; ++m) M = fma(B.Dmid[m], fo[m], M);
+    out[H] = M;
+  }
+}
+
+template <int DIM, int N, int EQ, typename real>
+struct StageGeom {
+  static constexpr int n = N + 1;
+  static constexpr int L = ipow_c(n, DIM - 1);      // lines per element along one axis
+  static constexpr int NPE = ipow_c(n, DIM);        // nodes per element
+  static constexpr int NV = EQ == 0 ? 1 : DIM + 1;  // variables
+  static constexpr int SPE = (n + 1) * L;           // padded shared slots per element
+  static constexpr int NS = EQ == 0 ? 2 * NV : 2 * NV + DIM;  // shared arrays of SPE per element
+  __device__ static __forceinline__ int pad(int node) { return node + node / n; }
+};
+
+template <int DIM, int N, int EQ, typename real>
+__global__ void stage_kernel(const StageArgs<real> args) {
+  using G = StageGeom<DIM, N, EQ, real>;
+  constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const GroupHeader hdr = *args.hdr;
+  const int epb = hdr.epb;
+  real* sU = reinterpret_cast<real*>(smem_raw);  // [NV][epb][SPE]
+  real* sR = sU + NV * epb * SPE;                 // [NV][epb][SPE]
+  real* sV = sR + NV * epb * SPE;                 // [DIM][epb][SPE] (Euler)
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+  const StagePlan& plan = args.plan;
+
+  for (int tile = blockIdx.x; tile < hdr.ntiles; tile += gridDim.x) {
+    // ---- which solve owns this tile (binary search over tile_begin) ----
+    int lo = 0, hi = hdr.nsolves - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (args.solves[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+    }
+    const SolveDesc* sd = args.solves + lo;
+    const long long nelem = sd->nelem;
+    const long long e0 = (long long)(tile - sd->tile_begin) * epb;
+    const int cnt = (int)min((long long)epb, nelem - e0);
+    const long long vstride = nelem * NPE;  // elements of one variable
+    const real* __restrict__ uin = static_cast<const real*>(sd->buf[plan.in]);
+
+    // ---- 1. tile of the stage input into shared memory ----
+    {
+      const int total = cnt * NPE;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const real* src = uin + v * vstride + e0 * NPE;
+        real* dst = sU + v * epb * SPE;
+        for (int idx = tid; idx < total; idx += nthr) {
+          const int el = idx / NPE, node = idx - el * NPE;
+          dst[el * SPE + G::pad(node)] = src[idx];
+        }
+      }
+    }
+    __syncthreads();
+    // ---- 2. velocities (Euler) ----
+    if constexpr (EQ == 1) {
+      const int total = cnt * NPE;
+      for (int idx = tid; idx < total; idx += nthr) {
+        const int el = idx / NPE, node = idx - el * NPE;
+        const int s = el * SPE + G::pad(node);
+        const real inv = real(1) / sU[s];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) sV[a * epb * SPE + s] = sU[(1 + a) * epb * SPE + s] * inv;
+      }
+      __syncthreads();
+    }
+    // ---- 3. volume + surface terms, axis by axis ----
+    const int E0 = sd->E[0], E1 = sd->E[1];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int el = tid / L;
+      const int line = tid - el * L;
+      if (el < cnt) {
+        // padded base / stride in shared memory; unpadded base / stride in global memory
+        int pbase, pstride, ubase, ustride;
+        if (a == 0) {
+          pbase = (n + 1) * line; pstride = 1; ubase = n * line; ustride = 1;
+        } else if (a == 1) {
+          const int i = line % n, k = line / n;
+          pbase = i + (n + 1) * n * k; pstride = n + 1; ubase = i + n * n * k; ustride = n;
+        } else {
+          pbase = line % n + (n + 1) * (line / n); pstride = (n + 1) * n; ubase = line; ustride = n * n;
+        }
+        // periodic neighbours along axis a
+        const long long e = e0 + el;
+        long long elo, ehi;
+        {
+          const long long ex = e % E0;
+          const long long rest = e / E0;
+          if (a == 0) {
+            elo = e - ex + (ex == 0 ? E0 - 1 : ex - 1);
+            ehi = e - ex + (ex == E0 - 1 ? 0 : ex + 1);
+          } else if (a == 1) {
+            const long long ey = rest % E1;
+            const long long step = E0;
+            elo = e + (ey == 0 ? (long long)(E1 - 1) * step : -step);
+            ehi = e + (ey == E1 - 1 ? -(long long)(E1 - 1) * step : step);
+          } else {
+            const long long ez = rest / E1;
+            const long long E2 = sd->E[2];
+            const long long step = (long long)E0 * E1;
+            elo = e + (ez == 0 ? (E2 - 1) * step : -step);
+            ehi = e + (ez == E2 - 1 ? -(E2 - 1) * step : step);
+          }
+        }
+        const bool lo_in = elo >= e0 && elo < e0 + cnt;
+        const bool hi_in = ehi >= e0 && ehi < e0 + cnt;
+        // exterior traces: node N of the low neighbour, node 0 of the high neighbour
+        real xlo[NV], xhi[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          xlo[v] = lo_in ? sU[(v * epb + (int)(elo - e0)) * SPE + pbase + N * pstride]
+                         : uin[v * vstride + elo * NPE + ubase + N * ustride];
+          xhi[v] = hi_in ? sU[(v * epb + (int)(ehi - e0)) * SPE + pbase]
+                         : uin[v * vstride + ehi * NPE + ubase];
+        }
+        const real* sUe = sU + el * SPE + pbase;
+        real* sRe = sR + el * SPE + pbase;
+        const real vs = (real)sd->vol_scale[a];
+        const real qlo = (real)sd->lift_lo[a];
+        const real qhi = (real)sd->lift_hi[a];
+        if constexpr (EQ == 0) {
+          real f[n], out[n];
+#pragma unroll
+          for (int l = 0; l < n; ++l) f[l] = sUe[l * pstride];
+          contract_even_odd<N>(f, out, args.basis);
+          const real slo = qlo * (xlo[0] - f[0]);
+          const real shi = qhi * (f[N] - xhi[0]);
+#pragma unroll
+          for (int l = 0; l < n; ++l) {
+            real r = (a == 0) ? vs * out[l] : fma(vs, out[l], sRe[l * pstride]);
+            if (l == 0) r += slo;
+            if (l == N) r += shi;
+            sRe[l * pstride] = r;
+          }
+        } else {
+          const real* sVa = sV + a * epb * SPE + el * SPE + pbase;
+          const real c2 = (real)sd->c2;
+          const real cs = (real)sd->c;
+          // normal velocities and LLF alpha at both faces of the line
+          const real un0 = sVa[0], unN = sVa[N * pstride];
+          const real unlo = xlo[1 + a] / xlo[0];
+          const real unhi = xhi[1 + a] / xhi[0];
+          const real alo = fmax(fabs(unlo), fabs(un0)) + cs;
+          const real ahi = fmax(fabs(unN), fabs(unhi)) + cs;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const real* sUv = sUe + v * epb * SPE;
+            real f[n], out[n];
+            // flux component v along a (Eq. (eulerIso2d)): v = 0: m_a; v = 1 + b: m_b u_a
+            // plus c^2 rho when b = a
+            if (v == 0) {
+              const real* sm = sUe + (1 + a) * epb * SPE;
+#pragma unroll
+              for (int l = 0; l < n; ++l) f[l] = sm[l * pstride];
+            } else if (v == 1 + a) {
+#pragma unroll
+              for (int l = 0; l < n; ++l)
+                f[l] = fma(sUv[l * pstride], sVa[l * pstride], c2 * sUe[l * pstride]);
+            } else {
+#pragma unroll
+              for (int l = 0; l < n; ++l) f[l] = sUv[l * pstride] * sVa[l * pstride];
+            }
+            contract_even_odd<N>(f, out, args.basis);
+            real fxlo, fxhi;
+            if (v == 0) {
+              fxlo = xlo[1 + a];
+              fxhi = xhi[1 + a];
+            } else if (v == 1 + a) {
+              fxlo = fma(xlo[v], unlo, c2 * xlo[0]);
+              fxhi = fma(xhi[v], unhi, c2 * xhi[0]);
+            } else {
+              fxlo = xlo[v] * unlo;
+              fxhi = xhi[v] * unhi;
+            }
+            const real u0 = sUv[0], uN = sUv[N * pstride];
+            // (Fhat_lo - F(U_0)) = 1/2 (F(ext) - F(U_0) - alpha (U_0 - ext)); qlo carries the 1/2
+            const real slo = qlo * (fxlo - f[0] - alo * (u0 - xlo[v]));
+            // (F(U_N) - Fhat_hi) = 1/2 (F(U_N) - F(ext) + alpha (ext - U_N))
+            const real shi = qhi * (f[N] - fxhi + ahi * (xhi[v] - uN));
+            real* sRv = sRe + v * epb * SPE;
+#pragma unroll
+            for (int l = 0; l < n; ++l) {
+              real r = (a == 0) ? vs * out[l] : fma(vs, out[l], sRv[l * pstride]);
+              if (l == 0) r += slo;
+              if (l == N) r += shi;
+              sRv[l * pstride] = r;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // ---- 4. Runge-Kutta stage update ----
+    {
+      const double dt = sd->dt;
+      const real a_self = (real)(plan.a_self * dt);
+      const real bdt = (real)(plan.b * dt);
+      real* __restrict__ uout = static_cast<real*>(sd->buf[plan.out]);
+      real* __restrict__ acc = static_cast<real*>(sd->buf[kACC]);
+      const real* __restrict__ un = static_cast<const real*>(sd->buf[kUN]);
+      real* __restrict__ kw = plan.kwrite >= 0 ? static_cast<real*>(sd->buf[plan.kwrite]) : nullptr;
+      const int total = cnt * NPE;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const real* sRv = sR + v * epb * SPE;
+        const real* sUv = sU + v * epb * SPE;
+        const long long goff = v * vstride + e0 * NPE;
+        for (int idx = tid; idx < total; idx += nthr) {
+          const int el = idx / NPE, node = idx - el * NPE;
+          const int s = el * SPE + G::pad(node);
+          const long long g = goff + idx;
+          const real r = sRv[s];
+          if (plan.acc_mode == 3) {
+            uout[g] = fma(bdt, r, acc[g]);
+            continue;
+          }
+          const real base = plan.in == kUN ? sUv[s] : un[g];
+          real o = fma(a_self, r, base);
+          for (int j = 0; j < plan.nread; ++j) {
+            const real* kj = static_cast<const real*>(sd->buf[plan.kread[j]]);
+            o = fma((real)(plan.a_read[j] * dt), kj[g], o);
+          }
+          uout[g] = o;
+          if (plan.acc_mode == 1) acc[g] = fma(bdt, r, base);
+          else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, acc[g]);
+          if (kw) kw[g] = r;  // the slope L(U_in); the combination above applies a*dt
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int DIM, int N, int EQ, typename real>
+void stage_shape(int epb, int* threads, size_t* smem) {
+  using G = StageGeom<DIM, N, EQ, real>;
+  *threads = epb * G::L;
+  *smem = (size_t)G::NS * epb * G::SPE * sizeof(real);
+}
+
+}  // namespace ndg

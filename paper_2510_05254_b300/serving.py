@@ -1,0 +1,152 @@
+"""Serving driver: a stream of independent solves arriving as a Poisson process, run either
+through the pool (ndg_pool_*: admission under a memory budget + continuous batching) or one at a
+time through a single context per solve (create, set_state, step, get_state, destroy).
+
+Latency = time the result is on the host - arrival time; throughput = solves / (last completion -
+first arrival).  All computation is libndg's; this module only schedules submissions.
+"""
+from __future__ import annotations
+
+import math
+import threading
+import time
+
+import numpy as np
+
+from . import inputs
+from . import native as nat
+
+CFL = 0.1
+
+
+def _coords(dim, degree, E):
+    """Node coordinates (dim, nelem, npe) on the unit box from the library's LGL nodes."""
+    xi, _ = nat.ndg_lgl(degree)
+    xi = np.asarray(xi)
+    n = degree + 1
+    axes = []
+    for a in range(dim):
+        h = 1.0 / E[a]
+        axes.append((np.arange(E[a])[:, None] * h + 0.5 * h * (xi[None, :] + 1.0)))  # (E, n)
+    if dim == 1:
+        return axes[0].reshape(1, E[0], n)
+    X = np.empty((2, E[1], E[0], n, n))
+    X[0] = axes[0][None, :, None, :]
+    X[1] = axes[1][:, None, :, None]
+    return X.reshape(2, E[0] * E[1], n * n)
+
+
+def prepare(requests, nsteps=100):
+    """Initial states and time steps of the serving workload (outside any timed region)."""
+    out = []
+    for r in requests:
+        E = (r["elems"], r["elems"])
+        X = _coords(2, r["degree"], E)
+        if r["equation"] == 0:
+            U = inputs.gaussian_noise(X, seed=r["seed"])
+            lam = 1.0 + 0.5
+        else:
+            U = inputs.euler_shear(X, seed=r["seed"])
+            lam = float(np.max(np.abs(U[1] / U[0]) + np.abs(U[2] / U[0]))) + 2.0
+        xi, _ = nat.ndg_lgl(r["degree"])
+        gap = min(xi[k + 1] - xi[k] for k in range(r["degree"]))
+        dt = CFL * (0.5 / r["elems"]) * gap / lam
+        U = np.ascontiguousarray(U, dtype=np.float64 if r["dtype"] == "f64" else np.float32)
+        out.append(dict(r, U=U, dt=dt, nsteps=nsteps))
+    return out
+
+
+def _cfg(r):
+    cfg = nat.ndg_config_init()
+    cfg.dim, cfg.degree = 2, r["degree"]
+    cfg.elems[0] = cfg.elems[1] = r["elems"]
+    cfg.equation = r["equation"]
+    cfg.flux = nat.NDG_FLUX_UPWIND if r["equation"] == 0 else nat.NDG_FLUX_LLF
+    cfg.velocity[0], cfg.velocity[1] = 1.0, 0.5
+    cfg.dtype = nat.NDG_F64 if r["dtype"] == "f64" else nat.NDG_F32
+    return cfg
+
+
+def _stats(lat, t_first, t_last, n):
+    lat = np.sort(np.asarray(lat))
+    return {"solves": n, "solves_per_s": n / max(t_last - t_first, 1e-9),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "wall_s": t_last - t_first}
+
+
+def run_pool(reqs, rate: float, budget_bytes: int, keep_results: bool = False):
+    """Submit at Poisson arrival times (rate solves/s; inf = all at once) and wait for all."""
+    pool = nat.ndg_pool_create(budget_bytes)
+    arrivals = _arrivals(reqs, rate)
+    tickets = [None] * len(reqs)
+    results = [None] * len(reqs)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            wait = arrivals[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets[i] = nat.ndg_pool_submit(pool, _cfg(r), r["U"].ctypes.data, r["U"].nbytes, 4, r["dt"],
+                                             r["nsteps"])
+
+    try:
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, first, last = [], math.inf, 0.0
+        for i, r in enumerate(reqs):
+            while tickets[i] is None:
+                time.sleep(1e-4)
+            out = np.empty_like(r["U"]) if keep_results else None
+            rc, st = nat.ndg_pool_poll(pool, tickets[i], out.ctypes.data if out is not None else None,
+                                       r["U"].nbytes if out is not None else 0, 3600.0)
+            assert rc == nat.NDG_OK
+            results[i] = out
+            lat.append(st.latency_s)
+            first, last = min(first, st.submit_s), max(last, st.done_s)
+        th.join()
+        status = nat.ndg_pool_status(pool)
+    finally:
+        nat.ndg_pool_destroy(pool)
+    s = _stats(lat, first, last, len(reqs))
+    s["peak_bytes"] = status["peak_bytes"]
+    s["budget_bytes"] = budget_bytes
+    return s, results
+
+
+def run_serial(reqs, rate: float, keep_results: bool = False):
+    """One solve at a time, in arrival order, each through its own context."""
+    import torch
+    arrivals = _arrivals(reqs, rate)
+    t0 = time.perf_counter()
+    lat, results = [], []
+    done_last = 0.0
+    for i, r in enumerate(reqs):
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        cfg = _cfg(r)
+        cfg.stream = torch.cuda.current_stream().cuda_stream
+        ctx = nat.ndg_create_ex(cfg)
+        try:
+            nat.ndg_set_state(ctx, r["U"].ctypes.data, r["U"].nbytes, False)
+            nat.ndg_step(ctx, r["dt"], r["nsteps"], 4)
+            out = np.empty_like(r["U"])
+            nat.ndg_get_state(ctx, out.ctypes.data, out.nbytes, False)
+        finally:
+            nat.ndg_destroy(ctx)
+        done = time.perf_counter() - t0
+        lat.append(done - arrivals[i])
+        done_last = done
+        results.append(out if keep_results else None)
+    return _stats(lat, 0.0, done_last, len(reqs)), results
+
+
+def _arrivals(reqs, rate):
+    if not math.isfinite(rate):
+        return [0.0] * len(reqs)
+    t, out = 0.0, []
+    for r in reqs:
+        t += r["gap"] / rate
+        out.append(t)
+    return out
