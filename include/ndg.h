@@ -167,6 +167,30 @@ int ndg_set_allocator(ndg_alloc_fn alloc, ndg_free_fn free_fn, void* user);
  * equation, dtype) for the process.  best_epb / best_ms may be NULL. */
 int ndg_autotune(ndg_ctx* ctx, int rk_scheme, int* best_epb, double* best_ms);
 
+/* Norms without any allocation.  The paper has no counterpart: this entry point exists for
+ * callers that may not allocate device memory -- for example an application that hands all of
+ * the GPU's memory to its own pool allocator at start-up, so that a cudaMalloc by a library
+ * either fails or breaks its accounting, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree may imply.
+ *   cfg describes the problem (dim, degree, elems, equation, dtype, length, velocity,
+ *       sound_speed, device; stream and elems_per_block are ignored);
+ *   U:   device pointer to the state in element layout, cfg->dtype;
+ *   ref: device pointer of the same shape or NULL (then the norms are of U itself);
+ *   nblocks: reduction blocks, 0 for the default 296, at most 1024;
+ *   out: device pointer to 8 doubles the caller owns, written with l2, linf, integral[0..3],
+ *        max_speed, nonfinite count (the ndg_norms_t fields in that order);
+ *   stream: cudaStream_t to enqueue on (NULL: the legacy default stream).
+ * Asynchronous: nothing waits for the GPU.  The per-block partial sums live in one file-scope
+ * device array of 1024 x 10 doubles (80 KiB) that every GPU which loads the library keeps until
+ * the process exits; no call allocates or frees anything.  The first call on a device looks the
+ * array's device address up (cudaGetSymbolAddress) -- make that first call before any stream
+ * capture.  All calls share the array: each call writes the partials it later reads, so nothing
+ * has to start at zero, but calls whose kernels overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Errors: NDG_EINVAL (bad cfg, NULL
+ * U/out, nblocks outside 0..1024), NDG_ECUDA. */
+int ndg_norms_noalloc(const ndg_config* cfg, const void* U, const void* ref, int nblocks, double* out,
+                      void* stream);
+
 /* ---- batching: several independent solves stepped together ------------------------------- */
 /* Group `n` contexts (all on the same device) into a batch.  One RK step of the batch is one
  * CUDA-graph replay in which every class of solve (dim, degree, equation, dtype) is one

@@ -6,7 +6,10 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 
+#include "../../include/ndg.h"
+#include "ndg_host.h"
 #include "ndg_internal.h"
 
 namespace ndg {
@@ -174,3 +177,70 @@ int launch_relayout(int dtype, int dim, int degree, int nvar, const int* E, cons
 }
 
 }  // namespace ndg
+
+// ------------------------------------------------------------------------------------------
+// ndg_norms_noalloc: the norms reduction with its per-block partial sums in a fixed,
+// file-scope device array instead of memory allocated by a context.
+// ------------------------------------------------------------------------------------------
+// Largest number of reduction blocks a call may use: kNoAllocMaxBlocks * kNormFields doubles
+// (80 KiB) that every GPU which loads this library keeps until the process exits.
+static constexpr int kNoAllocMaxBlocks = 1024;
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * ndg::kNormFields];
+
+namespace ndg {
+namespace {
+
+// Device address of g_noalloc_partials, looked up once per device with that device current.
+// In host code the symbol names a host-side stand-in, never the device memory itself.
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[64] = {nullptr};
+
+int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= 64) return fail(NDG_EINVAL, "device ordinal %d out of range", device);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    double* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static norms scratch");
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return NDG_OK;
+}
+
+}  // namespace
+}  // namespace ndg
+
+extern "C" int ndg_norms_noalloc(const ndg_config* cfg, const void* U, const void* ref, int nblocks,
+                                 double* out, void* stream) {
+  using namespace ndg;
+  if (!cfg || !U || !out) return fail(NDG_EINVAL, "cfg, U and out must not be NULL");
+  int rc = check_config(*cfg);
+  if (rc) return rc;
+  if (nblocks == 0) nblocks = kNormBlocks;
+  if (nblocks < 0 || nblocks > kNoAllocMaxBlocks)
+    return fail(NDG_EINVAL, "nblocks %d is outside 1..%d, the capacity of the static scratch", nblocks,
+                kNoAllocMaxBlocks);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != cfg->device) {
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  }
+  double* scratch = nullptr;
+  rc = noalloc_scratch(cfg->device, &scratch);
+  if (rc == NDG_OK) {
+    long long nelem = 1;
+    double jac = 1.0;
+    for (int a = 0; a < cfg->dim; ++a) {
+      nelem *= cfg->elems[a];
+      jac *= 0.5 * cfg->length[a] / cfg->elems[a];
+    }
+    cudaError_t e = (cudaError_t)launch_norms(cfg->dtype, cfg->dim, cfg->degree, cfg->equation, U, ref, nelem,
+                                              jac, cfg->sound_speed, cfg->velocity, nblocks, scratch, out,
+                                              stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "norms launch");
+  }
+  if (prev >= 0 && prev != cfg->device) cudaSetDevice(prev);
+  return rc;
+}

@@ -71,6 +71,7 @@ _SIGS = {
     "ndg_step": [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int],
     "ndg_norms": [_P, _P, ctypes.c_int, ctypes.POINTER(ndg_norms_t)],
     "ndg_stable_dt": [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+    "ndg_norms_noalloc": [ctypes.POINTER(ndg_config), _P, _P, ctypes.c_int, _P, _P],
     "ndg_node_coords": [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t],
     "ndg_info": [_P, ctypes.POINTER(ndg_info_t)],
     "ndg_lgl": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -176,6 +177,11 @@ def ndg_norms(ctx, ref_ptr=None, ref_on_device: bool = False, allow_nonfinite: b
     if rc != NDG_OK and not (allow_nonfinite and rc == NDG_ENONFINITE):
         raise NdgError(rc, "ndg_norms", ndg_last_error())
     return out
+
+
+def ndg_norms_noalloc(cfg: ndg_config, u_ptr: int, ref_ptr, nblocks: int, out_ptr: int, stream: int = 0) -> None:
+    """Norms into a caller-owned device buffer of 8 doubles, with no allocation by the library."""
+    _call("ndg_norms_noalloc", ctypes.byref(cfg), u_ptr, ref_ptr, int(nblocks), out_ptr, stream)
 
 
 def ndg_stable_dt(ctx, cfl: float) -> float:
