@@ -31,16 +31,33 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF-updates/s per RK stage (FP64 vs FP32); batched solves/s + p50/p99 latency"
-DIM, DEGREE, ELEMS, VEL, CFL, NSTEPS, RK = 2, 7, (256, 256), (1.0, 0.5, 0.0), 0.1, 1000, 4
+# The bench workload (default) and the two other full-size problems of the survey, selectable with
+# --workload: (dim, degree, elements, equation, velocity, RK steps per bench step, description).
+WORKLOADS = {
+    "adv2d": (2, 7, (256, 256), 0, (1.0, 0.5, 0.0), 1000,
+              "2D linear advection, 256x256 elements, degree 7 (8x8 LGL nodes), 4.19M DOF, RK4, 1000 steps"),
+    "euler2d": (2, 7, (512, 512), 1, (0.0, 0.0, 0.0), 200,
+                "2D isothermal Euler, 512x512 elements, degree 7, 3 x 4096^2 = 50.3M DOF, RK4, 200 steps"),
+    "euler3d": (3, 5, (64, 64, 64), 1, (0.0, 0.0, 0.0), 50,
+                "3D isothermal Euler, 64^3 elements, degree 5, 4 x 384^3 = 226.5M DOF, RK4, 50 steps"),
+}
+DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD = WORKLOADS["adv2d"]
+CFL, RK = 0.1, 4
 STAGES = 4
-WORKLOAD = "2D linear advection, 256x256 elements, degree 7 (8x8 LGL nodes), 4.19M DOF, RK4, 1000 steps"
 L2_FLUSH_BYTES = 256 << 20
 
-# Algorithmic work of one RK4 stage per DOF for 2D advection at degree 7:
-#   flops: sum-factorised strong-form volume term 2 axes x 8 FMA (32 flop) + per-axis scaling (3)
-#          + lifted face terms (1.5) + stage update (3.5 on average over the 4 stages) = 40 flop;
+
+def select_workload(name):
+    global DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD
+    DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD = WORKLOADS[name]
+
+# Algorithmic work of one RK4 stage per DOF:
+#   flops, 2D advection degree 7: sum-factorised strong-form volume term 2 axes x 8 FMA (32 flop)
+#          + per-axis scaling (3) + lifted face terms (1.5) + stage update (3.5 on average over the
+#          4 stages) = 40 flop; 2D isothermal Euler degree 7: 48; 3D isothermal Euler degree 5: 60;
 #   bytes: RK4 array passes per stage 3, 5, 5, 3 -> 4 on average x sizeof(real).
-FLOPS_PER_DOF_STAGE = 40.0
+FLOPS_PER_DOF = {"adv2d": 40.0, "euler2d": 48.0, "euler3d": 60.0}
+FLOPS_PER_DOF_STAGE = FLOPS_PER_DOF["adv2d"]
 PASSES_PER_STAGE = 4.0
 
 
@@ -141,13 +158,16 @@ def max_over_ranks(pg, x, dev):
 
 def initial_condition(X):
     from paper_2510_05254_b300 import inputs
-    return inputs.gaussian_noise(X)
+    if EQ == 0:
+        return inputs.gaussian_noise(X)
+    return inputs.euler_shear(X) if DIM == 2 else inputs.taylor_green(X)
 
 
 def oracle_sample(nsteps):
     """The FP64 oracle as it stands (single thread) on the full workload for nsteps RK4 steps."""
     from oracle import oracle as orc
-    p = orc.Problem(dim=DIM, degree=DEGREE, elems=ELEMS + (1,), equation=0, flux=0, velocity=VEL)
+    p = orc.Problem(dim=DIM, degree=DEGREE, elems=tuple(ELEMS) + (1,) * (3 - DIM), equation=EQ, flux=EQ,
+                    velocity=VEL)
     U0 = initial_condition(orc.node_coords(p))
     dt = orc.stable_dt(p, U0, CFL)
     t = time.perf_counter()
@@ -178,8 +198,9 @@ def run_reference(args, world, rank):
 
 
 def config_block(world):
-    return {"workload": WORKLOAD, "model": "NDG+RK4 2D linear advection (degree 7)", "global_batch": world,
-            "seq_len": None, "elements": list(ELEMS), "degree": DEGREE, "dof": 256 * 256 * 64,
+    ndof = (1 if EQ == 0 else DIM + 1) * int(np.prod(ELEMS)) * (DEGREE + 1) ** DIM
+    return {"workload": WORKLOAD, "model": f"NDG+RK4, dim {DIM}, degree {DEGREE}", "global_batch": world,
+            "seq_len": None, "elements": list(ELEMS), "degree": DEGREE, "dof": ndof,
             "rk_steps_per_bench_step": NSTEPS, "parallelism": f"replicas{world}",
             "l2": f"flushed at the start of every bench step ({L2_FLUSH_BYTES >> 20} MiB write, inside the timed region)"}
 
@@ -188,10 +209,11 @@ def run_solver_timed(dtype, args, dev, pg, U0_host):
     """Device-timed bench steps of one dtype: returns per-step device ms and stage-kernel ms."""
     import torch
     from paper_2510_05254_b300.solver import Solver
-    s = Solver(DIM, DEGREE, ELEMS, velocity=VEL, dtype=dtype, device=dev)
+    s = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype=dtype, device=dev)
     U0 = torch.tensor(U0_host, device=f"cuda:{dev}", dtype=s.torch_dtype)
     s.set_state(U0)
     dt = s.stable_dt(CFL)
+    epb, _ = s.autotune(RK)  # the library's tile autotuner (state is restored bitwise)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
     from paper_2510_05254_b300 import native as nat
 
@@ -222,7 +244,7 @@ def run_solver_timed(dtype, args, dev, pg, U0_host):
     barrier(pg, dev)
     total_ms = start.elapsed_time(end)
     stage_ms = sum(a.elapsed_time(b) for a, b in inner) / (args.steps * NSTEPS * STAGES)
-    out = {"total_ms": total_ms, "stage_ms": stage_ms, "ndof": s.ndof, "dt": dt, "clocks": clk.summary(),
+    out = {"total_ms": total_ms, "stage_ms": stage_ms, "ndof": s.ndof, "dt": dt, "clocks": clk.summary(), "epb": epb,
            "l2_norm": nr.l2, "mass": nr.integral[0], "state_bytes": s.state_bytes}
     s.close()
     return out
@@ -234,7 +256,7 @@ def run_e2e(args, dev, U0_host):
     import torch
     from paper_2510_05254_b300 import native as nat
     from paper_2510_05254_b300.solver import Solver
-    s = Solver(DIM, DEGREE, ELEMS, velocity=VEL, dtype="f64", device=dev)
+    s = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype="f64", device=dev)
     src = torch.tensor(U0_host, dtype=torch.float64).pin_memory()
     dst = torch.empty_like(src).pin_memory()
     s.set_state(U0_host)
@@ -283,7 +305,7 @@ def run_ours(args, world, rank, dev, pg):
     import torch
     from paper_2510_05254_b300.solver import Solver
     peaks, peak_kind = load_peaks()
-    probe = Solver(DIM, DEGREE, ELEMS, velocity=VEL, dtype="f64", device=dev)
+    probe = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype="f64", device=dev)
     X = probe.node_coords()
     probe.close()
     U0 = np.ascontiguousarray(initial_condition(X))
@@ -313,14 +335,17 @@ def run_ours(args, world, rank, dev, pg):
                 "d2h_bytes_per_step": nb + 8 * 8},
         "gpu_launches": args.steps * (NSTEPS * STAGES + 2),
         "roofline": {"bound": "alu", "achieved": ach64, "peak": p64, "unit": "TFLOP/s", "frac": ach64 / p64,
-                     "traffic": None, "kernel": "stage_kernel<2,7,adv,double>",
+                     "traffic": None, "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},double>",
                      "peak_note": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop at the max SM clock (derived)",
-                     "stage_ms": r64["stage_ms"]},
+                     "stage_ms": r64["stage_ms"], "elems_per_block": r64["epb"]},
         "f32": {"value": value32, "unit": "DOF-updates/s", "ms_per_step": t32 / args.steps,
                 "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
-                             "frac": ach32 / hbm, "traffic": None, "kernel": "stage_kernel<2,7,adv,float>",
+                             "frac": ach32 / hbm, "traffic": None, "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},float>",
                              "peak_kind": peak_kind, "stage_ms": r32["stage_ms"],
-                             "note": "working set 4 x 16.8 MB fits the 126 MB L2: stages after the first read L2"}},
+                             "elems_per_block": r32["epb"],
+                             "note": ("working set 4 x %.1f MB %s the 126 MB L2" % (
+                                 r32["state_bytes"] / 1e6,
+                                 "fits" if 4 * r32["state_bytes"] < 126e6 else "exceeds"))}},
         "clocks": r64["clocks"],
         "check": {"l2_norm_f64": r64["l2_norm"], "l2_norm_f32": r32["l2_norm"], "mass_f64": r64["mass"]},
     }
@@ -345,7 +370,13 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=15)
     ap.add_argument("--serving-solves", type=int, default=200)
     ap.add_argument("--serving-emax", type=int, default=512)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="adv2d")
     args = ap.parse_args()
+    select_workload(args.workload)
+    global FLOPS_PER_DOF_STAGE
+    FLOPS_PER_DOF_STAGE = FLOPS_PER_DOF[args.workload]
+    if args.workload != "adv2d":  # the roofline flop count and the CPU sample are the bench workload's
+        args.no_cpu_baseline = True
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local, pg = dist_setup(args)

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -283,8 +284,38 @@ std::map<long long, int> g_tuned;
 long long class_key(const KernelClass& k) {
   return ((long long)k.dim * 16 + k.degree) * 4 + k.equation * 2 + k.dtype;
 }
+// Optional persistent cache: NDG_AUTOTUNE_CACHE names a text file of lines
+// "dim degree equation dtype epb", read once per process and rewritten after each autotune.
+bool g_tune_loaded = false;
+void load_tune_cache_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("NDG_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int d, n, e, t, epb;
+  while (std::fscanf(f, "%d %d %d %d %d", &d, &n, &e, &t, &epb) == 5)
+    if (epb > 0 && epb <= 1024) g_tuned.emplace(class_key(KernelClass{d, n, e, t}), epb);
+  std::fclose(f);
+}
+void save_tune_cache_locked() {
+  const char* path = std::getenv("NDG_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  for (auto& kv : g_tuned) {
+    long long key = kv.first;
+    const int dtype = (int)(key % 2), eq = (int)((key / 2) % 2), deg = (int)((key / 4) % 16), dim = (int)(key / 64);
+    std::fprintf(f, "%d %d %d %d %d\n", dim, deg, eq, dtype, kv.second);
+  }
+  std::fclose(f);
+  std::rename(tmp.c_str(), path);
+}
 int tuned_epb(const KernelClass& k) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
+  load_tune_cache_locked();
   auto it = g_tuned.find(class_key(k));
   return it == g_tuned.end() ? 0 : it->second;
 }
@@ -361,6 +392,12 @@ void fill_solve_geometry(const ndg_config& cfg, const Basis& b, SolveDesc* dp) {
   }
   d.c = cfg.sound_speed;
   d.c2 = cfg.sound_speed * cfg.sound_speed;
+  d.rhs_scale = d.vol_scale[0] != 0.0 ? d.vol_scale[0] : 1.0;
+  for (int a = 0; a < 3; ++a) {
+    d.vol_scale[a] /= d.rhs_scale;
+    d.lift_lo[a] /= d.rhs_scale;
+    d.lift_hi[a] /= d.rhs_scale;
+  }
 }
 
 void fill_desc_geometry(ndg_ctx* c) { fill_solve_geometry(c->cfg, c->basis, &c->desc); }
@@ -869,7 +906,9 @@ int ndg_autotune(ndg_ctx* c, int rk, int* best_epb, double* best_ms) {
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_tune_cache_locked();
     g_tuned[class_key(c->kc)] = best;
+    save_tune_cache_locked();
   }
   if (best_epb) *best_epb = best;
   if (best_ms) *best_ms = best_t;

@@ -51,9 +51,12 @@ struct SolveDesc {
   int E[3];               // elements per axis (1 beyond dim)
   int tile_begin;         // first global tile index of this solve in the launch
   long long nelem;
-  double vol_scale[3];    // -2/h_a (Euler) or -2 a_a / h_a (advection): multiplies D F
-  double lift_lo[3];      // advection: (2/h_a)(1/w_0) (a_a + |a_a|)/2; Euler: (1/h_a)/w_0
-  double lift_hi[3];      // advection: (2/h_a)(1/w_N) (a_a - |a_a|)/2; Euler: (1/h_a)/w_N
+  // The kernel computes R' = L(U) / rhs_scale so that the first axis needs no multiply; the
+  // stage update multiplies its coefficients by rhs_scale.  rhs_scale = vol of axis 0 unless zero.
+  double rhs_scale;
+  double vol_scale[3];    // (-2/h_a (Euler) or -2 a_a / h_a (advection)) / rhs_scale, times D F
+  double lift_lo[3];      // advection: (2/h_a)(1/w_0) (a_a + |a_a|)/2; Euler: (1/h_a)/w_0; / rhs_scale
+  double lift_hi[3];      // advection: (2/h_a)(1/w_N) (a_a - |a_a|)/2; Euler: (1/h_a)/w_N; / rhs_scale
   double c2;              // c^2 (Euler)
   double c;               // c (Euler, LLF alpha)
   double dt;

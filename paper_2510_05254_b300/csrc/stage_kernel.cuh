@@ -188,35 +188,41 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         }
         const bool lo_in = elo >= e0 && elo < e0 + cnt;
         const bool hi_in = ehi >= e0 && ehi < e0 + cnt;
-        // exterior traces: node N of the low neighbour, node 0 of the high neighbour
-        real xlo[NV], xhi[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          xlo[v] = lo_in ? sU[(v * epb + (int)(elo - e0)) * SPE + pbase + N * pstride]
-                         : uin[v * vstride + elo * NPE + ubase + N * ustride];
-          xhi[v] = hi_in ? sU[(v * epb + (int)(ehi - e0)) * SPE + pbase]
-                         : uin[v * vstride + ehi * NPE + ubase];
-        }
         const real* sUe = sU + el * SPE + pbase;
         real* sRe = sR + el * SPE + pbase;
         const real vs = (real)sd->vol_scale[a];
         const real qlo = (real)sd->lift_lo[a];
         const real qhi = (real)sd->lift_hi[a];
+        // vs is exactly 1 on axis 0 unless the advection velocity has no x component
+        const bool unit = (a == 0) && vs == real(1);
         if constexpr (EQ == 0) {
+          // upwinding makes one of the two face terms vanish: its trace is not even loaded
+          const bool has_lo = qlo != real(0), has_hi = qhi != real(0);
+          real xlo = 0, xhi = 0;
+          if (has_lo)
+            xlo = lo_in ? sU[(int)(elo - e0) * SPE + pbase + N * pstride] : uin[elo * NPE + ubase + N * ustride];
+          if (has_hi) xhi = hi_in ? sU[(int)(ehi - e0) * SPE + pbase] : uin[ehi * NPE + ubase];
           real f[n], out[n];
 #pragma unroll
           for (int l = 0; l < n; ++l) f[l] = sUe[l * pstride];
           contract_even_odd<N>(f, out, args.basis);
-          const real slo = qlo * (xlo[0] - f[0]);
-          const real shi = qhi * (f[N] - xhi[0]);
 #pragma unroll
           for (int l = 0; l < n; ++l) {
-            real r = (a == 0) ? vs * out[l] : fma(vs, out[l], sRe[l * pstride]);
-            if (l == 0) r += slo;
-            if (l == N) r += shi;
+            real r = (a == 0) ? (unit ? out[l] : vs * out[l]) : fma(vs, out[l], sRe[l * pstride]);
+            if (l == 0 && has_lo) r = fma(qlo, xlo - f[0], r);
+            if (l == N && has_hi) r = fma(qhi, f[N] - xhi, r);
             sRe[l * pstride] = r;
           }
         } else {
+          // exterior traces: node N of the low neighbour, node 0 of the high neighbour
+          real xlo[NV], xhi[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            xlo[v] = lo_in ? sU[(v * epb + (int)(elo - e0)) * SPE + pbase + N * pstride]
+                           : uin[v * vstride + elo * NPE + ubase + N * ustride];
+            xhi[v] = hi_in ? sU[(v * epb + (int)(ehi - e0)) * SPE + pbase]
+                           : uin[v * vstride + ehi * NPE + ubase];
+          }
           const real* sVa = sV + a * epb * SPE + el * SPE + pbase;
           const real c2 = (real)sd->c2;
           const real cs = (real)sd->c;
@@ -257,16 +263,14 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               fxhi = xhi[v] * unhi;
             }
             const real u0 = sUv[0], uN = sUv[N * pstride];
-            // (Fhat_lo - F(U_0)) = 1/2 (F(ext) - F(U_0) - alpha (U_0 - ext)); qlo carries the 1/2
-            const real slo = qlo * (fxlo - f[0] - alo * (u0 - xlo[v]));
-            // (F(U_N) - Fhat_hi) = 1/2 (F(U_N) - F(ext) + alpha (ext - U_N))
-            const real shi = qhi * (f[N] - fxhi + ahi * (xhi[v] - uN));
             real* sRv = sRe + v * epb * SPE;
 #pragma unroll
             for (int l = 0; l < n; ++l) {
-              real r = (a == 0) ? vs * out[l] : fma(vs, out[l], sRv[l * pstride]);
-              if (l == 0) r += slo;
-              if (l == N) r += shi;
+              real r = (a == 0) ? (unit ? out[l] : vs * out[l]) : fma(vs, out[l], sRv[l * pstride]);
+              // (Fhat_lo - F(U_0)) = 1/2 (F(ext) - F(U_0) - alpha (U_0 - ext)); qlo carries the 1/2
+              if (l == 0) r = fma(qlo, fma(-alo, u0 - xlo[v], fxlo - f[0]), r);
+              // (F(U_N) - Fhat_hi) = 1/2 (F(U_N) - F(ext) + alpha (ext - U_N))
+              if (l == N) r = fma(qhi, fma(ahi, xhi[v] - uN, f[N] - fxhi), r);
               sRv[l * pstride] = r;
             }
           }
@@ -276,7 +280,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
     }
     // ---- 4. Runge-Kutta stage update ----
     {
-      const double dt = sd->dt;
+      const double dt = sd->dt * sd->rhs_scale;  // shared memory holds L(U) / rhs_scale
       const real a_self = (real)(plan.a_self * dt);
       const real bdt = (real)(plan.b * dt);
       real* __restrict__ uout = static_cast<real*>(sd->buf[plan.out]);
@@ -307,7 +311,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           uout[g] = o;
           if (plan.acc_mode == 1) acc[g] = fma(bdt, r, base);
           else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, acc[g]);
-          if (kw) kw[g] = r;  // the slope L(U_in); the combination above applies a*dt
+          if (kw) kw[g] = r;  // the slope L(U_in) / rhs_scale; the combination applies a*dt*rhs_scale
         }
       }
     }
