@@ -51,6 +51,12 @@ enum { NDG_FLUX_UPWIND = 0, NDG_FLUX_LLF = 1 };  /* Eq. (LF); upwind is valid fo
 enum { NDG_RK3 = 3, NDG_RK4 = 4, NDG_RK6 = 6 };  /* Eq. (RK3), Eq. (RK4), Eq. (RK6) */
 enum { NDG_F64 = 0, NDG_F32 = 1 };               /* state/arithmetic precision on the GPU */
 enum { NDG_LAYOUT_ELEMENT = 0, NDG_LAYOUT_GRID = 1 };
+/* Thread mapping of the stage kernel.  LINE = one thread per line of nodes, D applied through
+ * its even-odd halves (fewest FP64 operations); NODE = one thread per node, plain n-term sums,
+ * right-hand side in registers (fewest memory round trips).  The two round differently (both
+ * are within the parity tolerances); for a given mapping results do not depend on the tile size.
+ * AUTO = the autotuned choice for the kernel class, else LINE for FP64 and NODE for FP32. */
+enum { NDG_KERNEL_AUTO = 0, NDG_KERNEL_LINE = 1, NDG_KERNEL_NODE = 2 };
 
 typedef struct ndg_ctx ndg_ctx;     /* one solve: state, buffers, stream, launch plan */
 typedef struct ndg_batch ndg_batch; /* several solves stepped by one graph per RK step */
@@ -70,6 +76,7 @@ typedef struct {
   void* stream;       /* cudaStream_t to run on; NULL: the context creates its own */
   int elems_per_block;/* elements per CTA of the stage kernel; 0: library default */
   int device;         /* CUDA device ordinal; default 0 */
+  int kernel;         /* NDG_KERNEL_AUTO (default), NDG_KERNEL_LINE or NDG_KERNEL_NODE */
 } ndg_config;
 
 /* Norms by LGL quadrature on every element (Sec. 3.1's L2 norm). */
@@ -91,6 +98,7 @@ typedef struct {
   size_t state_bytes;  /* ndof * sizeof(real) */
   size_t device_bytes; /* device memory the context holds now */
   int elems_per_block; /* stage-kernel tile in use */
+  int kernel;          /* stage-kernel mapping in use: NDG_KERNEL_LINE or NDG_KERNEL_NODE */
 } ndg_info_t;
 
 /* Fill cfg with defaults: 2D, degree 7, 16x16 elements, advection, upwind, FP64, unit square,
@@ -162,9 +170,11 @@ typedef void* (*ndg_alloc_fn)(size_t bytes, void* user, void* stream);
 typedef void (*ndg_free_fn)(void* ptr, void* user, void* stream);
 int ndg_set_allocator(ndg_alloc_fn alloc, ndg_free_fn free_fn, void* user);
 
-/* Choose the stage kernel's elements per block for this context by timing the candidates on its
- * own state (which is restored bitwise afterwards).  Results are cached per (dim, degree,
- * equation, dtype) for the process.  best_epb / best_ms may be NULL. */
+/* Choose the stage kernel's elements per block and thread mapping for this context by timing
+ * the candidates on its own state (which is restored bitwise afterwards).  Results are cached
+ * per (dim, degree, equation, dtype) for the process, and in the text file named by the
+ * environment variable NDG_AUTOTUNE_CACHE when set.  best_epb / best_ms may be NULL; the mapping
+ * chosen is reported by ndg_info. */
 int ndg_autotune(ndg_ctx* ctx, int rk_scheme, int* best_epb, double* best_ms);
 
 /* Norms without any allocation.  The paper has no counterpart: this entry point exists for
@@ -193,11 +203,11 @@ int ndg_norms_noalloc(const ndg_config* cfg, const void* U, const void* ref, int
 
 /* ---- batching: several independent solves stepped together ------------------------------- */
 /* Group `n` contexts (all on the same device) into a batch.  One RK step of the batch is one
- * CUDA-graph replay in which every class of solve (dim, degree, equation, dtype) is one
- * persistent stage-kernel launch per stage over all of that class's solves, the classes running
- * as parallel branches.  The contexts stay owned by the caller and must outlive the batch; the
- * batch runs on the first context's stream.  Results are bitwise those of ndg_step on each
- * context alone. */
+ * CUDA-graph replay in which every class of solve (dim, degree, equation, dtype, kernel mapping)
+ * is one persistent stage-kernel launch per stage over all of that class's solves, the classes
+ * running as parallel branches.  The contexts stay owned by the caller and must outlive the
+ * batch; the batch runs on the first context's stream.  Results are bitwise those of ndg_step on
+ * each context alone. */
 int ndg_batch_create(ndg_ctx* const* ctxs, int n, ndg_batch** out);
 /* dts[i] is the step of context i; every context advances nsteps steps of scheme rk. */
 int ndg_batch_step(ndg_batch* b, const double* dts, int nsteps, int rk_scheme);

@@ -20,9 +20,9 @@
 
 namespace ndg {
 // per-(dtype, dim) dispatch tables from stage_<dtype>_d<dim>.cu
-using LaunchFn = int (*)(int, int, const SolveDesc*, const GroupHeader*, const StagePlan&, void*);
-using PrepareFn = int (*)(int, int*);
-using ShapeFn = void (*)(int, int*, size_t*);
+using LaunchFn = int (*)(int, int, int, const SolveDesc*, const GroupHeader*, const StagePlan&, void*);
+using PrepareFn = int (*)(int, int, int*);
+using ShapeFn = void (*)(int, int, int*, size_t*);
 #define NDG_DECL(tag)                         \
   LaunchFn tag##_launch(int degree, int eq);  \
   PrepareFn tag##_prepare(int degree, int eq); \
@@ -54,21 +54,21 @@ ShapeFn pick_shape(const KernelClass& k) {
 }
 }  // namespace
 
-int launch_stage(const KernelClass& kc, int grid, int epb, const SolveDesc* solves,
+int launch_stage(const KernelClass& kc, int variant, int grid, int epb, const SolveDesc* solves,
                  const GroupHeader* header, const StagePlan& plan, void* stream) {
   LaunchFn f = pick_launch(kc);
   if (!f) return (int)cudaErrorInvalidValue;
-  return f(grid, epb, solves, header, plan, stream);
+  return f(variant, grid, epb, solves, header, plan, stream);
 }
 
-void stage_launch_shape(const KernelClass& kc, int epb, int* threads, size_t* smem) {
-  pick_shape(kc)(epb, threads, smem);
+void stage_launch_shape(const KernelClass& kc, int variant, int epb, int* threads, size_t* smem) {
+  pick_shape(kc)(variant, epb, threads, smem);
 }
 
-int prepare_stage_kernel(const KernelClass& kc, int epb, int* max_blocks) {
+int prepare_stage_kernel(const KernelClass& kc, int variant, int epb, int* max_blocks) {
   PrepareFn f = pick_prepare(kc);
   if (!f) return (int)cudaErrorInvalidValue;
-  return f(epb, max_blocks);
+  return f(variant, epb, max_blocks);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -86,8 +86,20 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+thread_local std::string g_launch_detail;
+
+void launch_error_detail(int grid, int threads, size_t smem, int max_threads, int regs, size_t local,
+                         int max_dyn_smem) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), " (grid %d, block %d, dynamic smem %zu; kernel: max block %d, %d registers, "
+           "%zu B local, max dynamic smem %d)", grid, threads, smem, max_threads, regs, local, max_dyn_smem);
+  g_launch_detail = buf;
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
-  return fail(NDG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  std::string detail;
+  detail.swap(g_launch_detail);
+  return fail(NDG_ECUDA, "%s: %s%s", what, cudaGetErrorString(e), detail.c_str());
 }
 
 // ------------------------------------------------------------------------------------------
@@ -191,6 +203,7 @@ const std::vector<StagePlan>& stage_plans(int rk) {
           if (A[st + 1][j] == 0.0) continue;
           sp.kread[sp.nread] = kK0 + j;
           sp.a_read[sp.nread] = A[st + 1][j];
+          sp.a_read_f[sp.nread] = (float)A[st + 1][j];
           ++sp.nread;
         }
         // k_{st+1} is needed later if any later stage input (rows > st+1) uses it
@@ -240,7 +253,7 @@ int group_upload(Group& g, cudaStream_t stream) {
     if (e != cudaSuccess) return cuda_fail(e, "alloc solve descriptors");
     g.cap = cap;
   }
-  GroupHeader h{(int)g.h_desc.size(), g.ntiles, g.epb, 0};
+  GroupHeader h{(int)g.h_desc.size(), g.ntiles, g.epb, g.variant};
   cudaError_t e = cudaMemcpyAsync(g.d_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess && !g.h_desc.empty())
     e = cudaMemcpyAsync(g.d_desc, g.h_desc.data(), g.h_desc.size() * sizeof(SolveDesc),
@@ -268,24 +281,47 @@ int num_sms(int device) {
   return cached[device];
 }
 
-int default_epb(const KernelClass& kc) {
-  // about 128-256 threads per CTA: lines per element = n^(dim-1)
+int default_epb_for(const KernelClass& kc, int variant) {
   const int n = kc.degree + 1;
+  if (variant == kNodeKernel) {  // node-per-thread kernel: about 256 threads per CTA
+    int npe = 1;
+    for (int d = 0; d < kc.dim; ++d) npe *= n;
+    return std::max(1, 256 / npe);
+  }
+  // line-per-thread kernel: about 128-256 threads per CTA (lines per element = n^(dim-1)), and
+  // at most ~100 KB of shared memory so that two CTAs fit on an SM
   int L = 1;
   for (int d = 1; d < kc.dim; ++d) L *= n;
   int epb = std::max(1, 256 / L);
   if (kc.dim == 3) epb = std::max(1, 192 / L);
-  return std::min(epb, 64);
+  epb = std::min(epb, 64);
+  while (epb > 1) {
+    int threads;
+    size_t smem;
+    stage_launch_shape(kc, variant, epb, &threads, &smem);
+    if (smem <= 100 * 1024) break;
+    --epb;
+  }
+  return epb;
 }
 
-// Autotuned tile sizes per class for this process.
+// Untuned choice: the line kernel (fewest FP64 operations) for FP64, the node kernel (fewest
+// memory round trips) for FP32.
+TileConfig default_tile(const KernelClass& kc) {
+  TileConfig t;
+  t.variant = kc.dtype == NDG_F32 ? kNodeKernel : kLineKernel;
+  t.epb = default_epb_for(kc, t.variant);
+  return t;
+}
+
+// Autotuned tiles per class for this process.
 std::mutex g_tune_mu;
-std::map<long long, int> g_tuned;
+std::map<long long, TileConfig> g_tuned;
 long long class_key(const KernelClass& k) {
   return ((long long)k.dim * 16 + k.degree) * 4 + k.equation * 2 + k.dtype;
 }
 // Optional persistent cache: NDG_AUTOTUNE_CACHE names a text file of lines
-// "dim degree equation dtype epb", read once per process and rewritten after each autotune.
+// "dim degree equation dtype epb variant", read once per process, rewritten after each autotune.
 bool g_tune_loaded = false;
 void load_tune_cache_locked() {
   if (g_tune_loaded) return;
@@ -294,9 +330,10 @@ void load_tune_cache_locked() {
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int d, n, e, t, epb;
-  while (std::fscanf(f, "%d %d %d %d %d", &d, &n, &e, &t, &epb) == 5)
-    if (epb > 0 && epb <= 1024) g_tuned.emplace(class_key(KernelClass{d, n, e, t}), epb);
+  int d, n, e, t, epb, var;
+  while (std::fscanf(f, "%d %d %d %d %d %d", &d, &n, &e, &t, &epb, &var) == 6)
+    if (epb > 0 && epb <= 1024 && (var == kLineKernel || var == kNodeKernel))
+      g_tuned.emplace(class_key(KernelClass{d, n, e, t}), TileConfig{epb, var});
   std::fclose(f);
 }
 void save_tune_cache_locked() {
@@ -308,16 +345,16 @@ void save_tune_cache_locked() {
   for (auto& kv : g_tuned) {
     long long key = kv.first;
     const int dtype = (int)(key % 2), eq = (int)((key / 2) % 2), deg = (int)((key / 4) % 16), dim = (int)(key / 64);
-    std::fprintf(f, "%d %d %d %d %d\n", dim, deg, eq, dtype, kv.second);
+    std::fprintf(f, "%d %d %d %d %d %d\n", dim, deg, eq, dtype, kv.second.epb, kv.second.variant);
   }
   std::fclose(f);
   std::rename(tmp.c_str(), path);
 }
-int tuned_epb(const KernelClass& k) {
+TileConfig tuned_tile(const KernelClass& k) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   load_tune_cache_locked();
   auto it = g_tuned.find(class_key(k));
-  return it == g_tuned.end() ? 0 : it->second;
+  return it == g_tuned.end() ? TileConfig{} : it->second;
 }
 
 }  // namespace ndg
@@ -335,12 +372,12 @@ struct ndg_ctx {
   bool have_state = false;
   double t = 0.0;
   long long steps = 0;
-  int epb = 0;
+  TileConfig tile;
   Basis basis;
   SolveDesc desc;  // this solve's descriptor (buffers, geometry, dt)
   Group group;     // the solve alone as a launch group
   cudaGraphExec_t graph[7] = {nullptr};
-  int graph_epb[7] = {0};
+  TileConfig graph_tile[7];
   double* d_partials = nullptr;
   double* d_result = nullptr;
   double* h_result = nullptr;  // pinned
@@ -397,7 +434,12 @@ void fill_solve_geometry(const ndg_config& cfg, const Basis& b, SolveDesc* dp) {
     d.vol_scale[a] /= d.rhs_scale;
     d.lift_lo[a] /= d.rhs_scale;
     d.lift_hi[a] /= d.rhs_scale;
+    d.f_vol_scale[a] = (float)d.vol_scale[a];
+    d.f_lift_lo[a] = (float)d.lift_lo[a];
+    d.f_lift_hi[a] = (float)d.lift_hi[a];
   }
+  d.f_c = (float)d.c;
+  d.f_c2 = (float)d.c2;
 }
 
 void fill_desc_geometry(ndg_ctx* c) { fill_solve_geometry(c->cfg, c->basis, &c->desc); }
@@ -410,17 +452,18 @@ void drop_graphs(ndg_ctx* c) {
     }
 }
 
-int set_group_epb(ndg_ctx* c, int epb) {
+int set_group_tile(ndg_ctx* c, TileConfig t) {
   int maxb = 0;
-  int e = prepare_stage_kernel(c->kc, epb, &maxb);
+  int e = prepare_stage_kernel(c->kc, t.variant, t.epb, &maxb);
   if (e != 0 || maxb < 1)
-    return fail(NDG_EINVAL, "elems_per_block %d does not fit this kernel class (%s)", epb,
+    return fail(NDG_EINVAL, "elems_per_block %d does not fit this kernel class (%s)", t.epb,
                 e ? cudaGetErrorString((cudaError_t)e) : "no resident CTA");
-  c->epb = epb;
+  c->tile = t;
   Group& g = c->group;
   g.kc = c->kc;
-  g.epb = epb;
-  g.ntiles = (int)((c->nelem + epb - 1) / epb);
+  g.epb = t.epb;
+  g.variant = t.variant;
+  g.ntiles = (int)((c->nelem + t.epb - 1) / t.epb);
   c->desc.tile_begin = 0;
   g.grid = std::min(g.ntiles, maxb * num_sms(c->cfg.device));
   g.h_desc.assign(1, c->desc);
@@ -449,7 +492,7 @@ int capture_step(const std::vector<Group*>& groups, int rk, cudaStream_t cap, cu
       cudaStream_t s = side[i];
       cudaStreamWaitEvent(s, ev[groups.size()], 0);
       for (const StagePlan& p : plans) {
-        int le = launch_stage(g->kc, std::max(1, g->grid), g->epb, g->d_desc, g->d_hdr, p, s);
+        int le = launch_stage(g->kc, g->variant, std::max(1, g->grid), g->epb, g->d_desc, g->d_hdr, p, s);
         if (le != 0 && rc == NDG_OK) rc = cuda_fail((cudaError_t)le, "stage launch");
       }
       cudaEventRecord(ev[i], s);
@@ -494,6 +537,8 @@ int check_config(const ndg_config& k) {
   if (k.equation == NDG_ISO_EULER && !(k.sound_speed > 0.0 && std::isfinite(k.sound_speed)))
     return fail(NDG_EINVAL, "sound speed must be positive");
   if (k.elems_per_block < 0) return fail(NDG_EINVAL, "elems_per_block must be >= 0");
+  if (k.kernel != NDG_KERNEL_AUTO && k.kernel != NDG_KERNEL_LINE && k.kernel != NDG_KERNEL_NODE)
+    return fail(NDG_EINVAL, "unknown kernel mapping %d", k.kernel);
   return NDG_OK;
 }
 
@@ -560,6 +605,7 @@ int ndg_create_ex(const ndg_config* cfg, ndg_ctx** out) {
   }
   long long nelem = 1;
   for (int a = 0; a < k.dim; ++a) nelem *= k.elems[a];
+  if (nelem > 0x7fffffffLL) return fail(NDG_EINVAL, "more than 2^31 - 1 elements");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
     return fail(NDG_ECUDA, "no CUDA device available");
@@ -608,10 +654,14 @@ int ndg_create_ex(const ndg_config* cfg, ndg_ctx** out) {
     if (e != cudaSuccess) rc = fail(NDG_ENOMEM, "norm buffers: %s", cudaGetErrorString(e));
   }
   if (rc == NDG_OK) {
-    int epb = k.elems_per_block ? k.elems_per_block : tuned_epb(c->kc);
-    if (!epb) epb = default_epb(c->kc);
-    epb = (int)std::min<long long>(epb, nelem);
-    rc = set_group_epb(c, epb);
+    TileConfig t = tuned_tile(c->kc);
+    if (!t.epb) t = default_tile(c->kc);
+    if (k.kernel == NDG_KERNEL_LINE) t.variant = kLineKernel;
+    if (k.kernel == NDG_KERNEL_NODE) t.variant = kNodeKernel;
+    if (k.kernel != NDG_KERNEL_AUTO && !k.elems_per_block) t.epb = default_epb_for(c->kc, t.variant);
+    if (k.elems_per_block) t.epb = k.elems_per_block;
+    t.epb = (int)std::min<long long>(t.epb, nelem);
+    rc = set_group_tile(c, t);
   }
   if (rc != NDG_OK) {
     std::string msg = g_last_error;
@@ -643,7 +693,8 @@ int ndg_info(const ndg_ctx* c, ndg_info_t* o) {
   o->ndof = c->ndof;
   o->state_bytes = c->state_bytes;
   o->device_bytes = c->device_bytes;
-  o->elems_per_block = c->epb;
+  o->elems_per_block = c->tile.epb;
+  o->kernel = c->tile.variant == kNodeKernel ? NDG_KERNEL_NODE : NDG_KERNEL_LINE;
   return NDG_OK;
 }
 
@@ -750,7 +801,7 @@ int ndg_step(ndg_ctx* c, double dt, int nsteps, int rk) {
     if (rc) return rc;
   }
   cudaGraphExec_t& ge = c->graph[rk];
-  if (!ge || c->graph_epb[rk] != c->epb) {
+  if (!ge || c->graph_tile[rk].epb != c->tile.epb || c->graph_tile[rk].variant != c->tile.variant) {
     if (ge) {
       cudaGraphExecDestroy(ge);
       ge = nullptr;
@@ -764,7 +815,7 @@ int ndg_step(ndg_ctx* c, double dt, int nsteps, int rk) {
     cudaEventDestroy(ev);
     rc = capture_step(groups, rk, c->capture_stream, &ge);
     if (rc) return rc;
-    c->graph_epb[rk] = c->epb;
+    c->graph_tile[rk] = c->tile;
   }
   for (int s = 0; s < nsteps; ++s) {
     cudaError_t e = cudaGraphLaunch(ge, c->stream);
@@ -861,42 +912,46 @@ int ndg_autotune(ndg_ctx* c, int rk, int* best_epb, double* best_ms) {
   // a tiny step keeps the state bounded while timing
   double dt = 1e-6;
   const int cands[] = {1, 2, 4, 8, 16, 32, 64};
-  int best = c->epb;
+  TileConfig best = c->tile;
   double best_t = 1e300;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  const int orig = c->epb;
-  for (int epb : cands) {
-    if (epb > c->nelem) break;
-    int threads;
-    size_t smem;
-    stage_launch_shape(c->kc, epb, &threads, &smem);
-    if (threads > 1024 || threads < 32 || smem > 220 * 1024) continue;
-    {
-      std::lock_guard<std::mutex> lk(c->mu);
-      if (set_group_epb(c, epb) != NDG_OK) continue;
-    }
-    const long long dofs = c->ndof;
-    const int reps = (int)std::max<long long>(2, std::min<long long>(50, 400000000LL / std::max<long long>(1, dofs)));
-    if (ndg_step(c, dt, 1, rk) != NDG_OK) continue;  // warm-up + capture
-    cudaEventRecord(a, c->stream);
-    ndg_step(c, dt, reps, rk);
-    cudaEventRecord(b, c->stream);
-    cudaEventSynchronize(b);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    const double per = ms / reps;
-    if (per < best_t) {
-      best_t = per;
-      best = epb;
+  const TileConfig orig = c->tile;
+  for (int variant : {kLineKernel, kNodeKernel}) {
+    if (c->cfg.kernel == NDG_KERNEL_LINE && variant != kLineKernel) continue;
+    if (c->cfg.kernel == NDG_KERNEL_NODE && variant != kNodeKernel) continue;
+    for (int epb : cands) {
+      if (epb > c->nelem) break;
+      int threads;
+      size_t smem;
+      stage_launch_shape(c->kc, variant, epb, &threads, &smem);
+      if (threads > 1024 || threads < 32 || smem > 220 * 1024) continue;
+      {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (set_group_tile(c, TileConfig{epb, variant}) != NDG_OK) continue;
+      }
+      const long long dofs = c->ndof;
+      const int reps = (int)std::max<long long>(2, std::min<long long>(50, 400000000LL / std::max<long long>(1, dofs)));
+      if (ndg_step(c, dt, 1, rk) != NDG_OK) continue;  // warm-up + capture
+      cudaEventRecord(a, c->stream);
+      ndg_step(c, dt, reps, rk);
+      cudaEventRecord(b, c->stream);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      const double per = ms / reps;
+      if (per < best_t) {
+        best_t = per;
+        best = TileConfig{epb, variant};
+      }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   {
     std::lock_guard<std::mutex> lk(c->mu);
-    rc = set_group_epb(c, best ? best : orig);
+    rc = set_group_tile(c, best.epb ? best : orig);
     cudaMemcpyAsync(c->buf[kUN], save, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
     cudaStreamSynchronize(c->stream);
   }
@@ -910,7 +965,7 @@ int ndg_autotune(ndg_ctx* c, int rk, int* best_epb, double* best_ms) {
     g_tuned[class_key(c->kc)] = best;
     save_tune_cache_locked();
   }
-  if (best_epb) *best_epb = best;
+  if (best_epb) *best_epb = best.epb;
   if (best_ms) *best_ms = best_t;
   return NDG_OK;
 }
@@ -992,11 +1047,12 @@ int ndg_batch_create(ndg_ctx* const* ctxs, int n, ndg_batch** out) {
     const KernelClass& kc = ctxs[i]->kc;
     size_t gi = 0;
     for (; gi < b->groups.size(); ++gi)
-      if (b->groups[gi].kc == kc) break;
+      if (b->groups[gi].kc == kc && b->groups[gi].variant == ctxs[i]->tile.variant) break;
     if (gi == b->groups.size()) {
       Group g;
       g.kc = kc;
-      g.epb = ctxs[i]->epb;
+      g.epb = ctxs[i]->tile.epb;
+      g.variant = ctxs[i]->tile.variant;
       b->groups.push_back(g);
       b->members.push_back({});
     }
@@ -1004,7 +1060,7 @@ int ndg_batch_create(ndg_ctx* const* ctxs, int n, ndg_batch** out) {
   }
   for (Group& g : b->groups) {
     int maxb = 0;
-    int pe = prepare_stage_kernel(g.kc, g.epb, &maxb);
+    int pe = prepare_stage_kernel(g.kc, g.variant, g.epb, &maxb);
     if (pe != 0 || maxb < 1) {
       ndg_batch_destroy(b);
       return fail(NDG_EINVAL, "tile does not fit");

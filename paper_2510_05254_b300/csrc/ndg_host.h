@@ -26,6 +26,7 @@ bool valid_rk(int rk);
 // Launch resources of one kernel class over a set of solves (one persistent launch per stage).
 struct Group {
   KernelClass kc{};
+  int variant = 0;  // kLineKernel / kNodeKernel
   int epb = 0;
   int grid = 0;
   int ntiles = 0;
@@ -40,8 +41,13 @@ void group_free(Group& g, cudaStream_t stream);
 int capture_step(const std::vector<Group*>& groups, int rk, cudaStream_t cap, cudaGraphExec_t* out);
 
 int num_sms(int device);
-int default_epb(const KernelClass& kc);
-int tuned_epb(const KernelClass& kc);
+// Stage-kernel tile: elements per CTA and thread mapping.
+struct TileConfig {
+  int epb = 0;
+  int variant = 0;
+};
+TileConfig default_tile(const KernelClass& kc);
+TileConfig tuned_tile(const KernelClass& kc);  // epb == 0 when the class was never tuned
 
 // Geometry part of a solve descriptor (scales, lift coefficients, element counts).
 void fill_solve_geometry(const ndg_config& cfg, const Basis& b, SolveDesc* d);

@@ -40,6 +40,7 @@ struct StagePlan {
   int nread;      // number of stored slopes in the stage combination
   int kread[kMaxStages];
   double a_read[kMaxStages];
+  float a_read_f[kMaxStages];  // FP32 copies of a_read (for the FP32 kernels)
   double a_self;
   int acc_mode;
   double b;
@@ -60,6 +61,9 @@ struct SolveDesc {
   double c2;              // c^2 (Euler)
   double c;               // c (Euler, LLF alpha)
   double dt;
+  // FP32 copies of the geometric coefficients above (an FP32 kernel must not spend FP64
+  // operations -- 1/64 of the FP32 rate on B300 -- converting them per node)
+  float f_vol_scale[3], f_lift_lo[3], f_lift_hi[3], f_c2, f_c;
 };
 
 // Header of a launch's work list (device memory): tiles are numbered across all solves.
@@ -67,8 +71,13 @@ struct GroupHeader {
   int nsolves;
   int ntiles;
   int epb;                // elements per CTA tile
-  int pad;
+  int variant;            // kernel mapping: kLineKernel or kNodeKernel
 };
+
+// Kernel mappings of one stage (same arithmetic per element, different thread mapping):
+// kLineKernel: one thread per line of n nodes, even-odd D (fewest FP64 operations);
+// kNodeKernel: one thread per node, right-hand side in registers (fewest memory round trips).
+enum { kLineKernel = 0, kNodeKernel = 1 };
 
 // Kernel class: everything that is a template parameter of the stage kernel.
 struct KernelClass {
@@ -80,12 +89,15 @@ struct KernelClass {
 
 // Launch one RK stage of the fused kernel for a group: `grid` CTAs loop over the group's tiles.
 // Returns a cudaError_t value.
-int launch_stage(const KernelClass& kc, int grid, int epb, const SolveDesc* solves,
+int launch_stage(const KernelClass& kc, int variant, int grid, int epb, const SolveDesc* solves,
                  const GroupHeader* header, const StagePlan& plan, void* stream);
-// Threads and dynamic shared memory of one CTA for a class and tile size.
-void stage_launch_shape(const KernelClass& kc, int epb, int* threads, size_t* smem_bytes);
+// Records the shape of a failed stage launch; appended to the next error message.
+void launch_error_detail(int grid, int threads, size_t smem, int max_threads, int regs, size_t local,
+                         int max_dyn_smem);
+// Threads and dynamic shared memory of one CTA for a class, mapping and tile size.
+void stage_launch_shape(const KernelClass& kc, int variant, int epb, int* threads, size_t* smem_bytes);
 // Ensure the kernel's attributes (max dynamic smem) are set; returns cudaError_t.
-int prepare_stage_kernel(const KernelClass& kc, int epb, int* max_blocks_per_sm);
+int prepare_stage_kernel(const KernelClass& kc, int variant, int epb, int* max_blocks_per_sm);
 
 // Upload the basis of every degree to constant memory on the current device (idempotent).
 int upload_bases();

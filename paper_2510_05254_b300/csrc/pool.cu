@@ -115,12 +115,13 @@ int rebuild_lists(ndg_pool* p) {
       PoolClass pc;
       pc.rk = s->rk;
       pc.group.kc = s->kc;
-      int epb = tuned_epb(s->kc);
-      if (!epb) epb = default_epb(s->kc);
+      TileConfig t = tuned_tile(s->kc);
+      if (!t.epb) t = default_tile(s->kc);
       int maxb = 0;
-      int e = prepare_stage_kernel(s->kc, epb, &maxb);
+      int e = prepare_stage_kernel(s->kc, t.variant, t.epb, &maxb);
       if (e != 0 || maxb < 1) return fail(NDG_ECUDA, "stage kernel does not fit");
-      pc.group.epb = epb;
+      pc.group.epb = t.epb;
+      pc.group.variant = t.variant;
       pc.group.grid = maxb * num_sms(p->device);
       it = p->classes.emplace(key, std::move(pc)).first;
       p->graph_dirty = true;
@@ -186,7 +187,8 @@ int launch_step(ndg_pool* p) {
         Group* gr = kv.second[i];
         cudaStreamWaitEvent(side[i], evs.back(), 0);
         for (const StagePlan& sp : plans) {
-          int le = launch_stage(gr->kc, std::max(1, gr->grid), gr->epb, gr->d_desc, gr->d_hdr, sp, side[i]);
+          int le = launch_stage(gr->kc, gr->variant, std::max(1, gr->grid), gr->epb, gr->d_desc, gr->d_hdr, sp,
+                                side[i]);
           if (le && rc == NDG_OK) rc = cuda_fail((cudaError_t)le, "stage launch");
         }
         cudaEventRecord(evs[i], side[i]);
@@ -418,6 +420,9 @@ int ndg_pool_submit(ndg_pool* p, const ndg_config* cfg, const void* u0, size_t n
   const int n = cfg->degree + 1;
   long long ndof = cfg->equation == NDG_ADVECTION ? 1 : cfg->dim + 1;
   for (int a = 0; a < cfg->dim; ++a) ndof *= (long long)cfg->elems[a] * n;
+  long long nelem = 1;
+  for (int a = 0; a < cfg->dim; ++a) nelem *= cfg->elems[a];
+  if (nelem > 0x7fffffffLL) return fail(NDG_EINVAL, "more than 2^31 - 1 elements");
   s->state_bytes = (size_t)ndof * (cfg->dtype == NDG_F64 ? 8 : 4);
   if (nbytes != s->state_bytes)
     return fail(NDG_EINVAL, "state size mismatch: got %zu bytes, expected %zu", nbytes, s->state_bytes);

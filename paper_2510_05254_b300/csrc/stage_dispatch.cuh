@@ -2,8 +2,10 @@
 // both equations.  Each stage_<dtype>_d<dim>.cu includes this with NDG_REAL / NDG_DIM defined.
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "stage_kernel.cuh"
+#include "stage_np_kernel.cuh"
 
 namespace ndg {
 
@@ -20,6 +22,7 @@ const BasisArgs<real>& basis_args(int N) {
       BasisArgs<real>& t = table[d];
       std::memset(&t, 0, sizeof(t));
       const int n = d + 1, h = n / 2;
+      for (int i = 0; i < n * n; ++i) t.D[i] = (real)b.D[i];
       for (int i = 0; i < h; ++i)
         for (int m = 0; m < h; ++m) {
           t.Ae[i * 4 + m] = (real)b.Ae[i * kMaxN + m];
@@ -34,8 +37,16 @@ const BasisArgs<real>& basis_args(int N) {
   return table[N];
 }
 
+// Two thread mappings of the same stage (see kLineKernel / kNodeKernel); the tile autotuner
+// picks one per kernel class.
 template <int N, int EQ>
-int launch_one(int grid, int epb, const SolveDesc* solves, const GroupHeader* header,
+void shape_of(int variant, int epb, int* threads, size_t* smem) {
+  if (variant == kNodeKernel) stage_np_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, threads, smem);
+  else stage_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, threads, smem);
+}
+
+template <int N, int EQ>
+int launch_one(int variant, int grid, int epb, const SolveDesc* solves, const GroupHeader* header,
                const StagePlan& plan, void* stream) {
   StageArgs<NDG_REAL> args;
   args.solves = solves;
@@ -44,18 +55,32 @@ int launch_one(int grid, int epb, const SolveDesc* solves, const GroupHeader* he
   args.basis = basis_args<NDG_REAL>(N);
   int threads;
   size_t smem;
-  stage_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, &threads, &smem);
-  stage_kernel<NDG_DIM, N, EQ, NDG_REAL><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
-  return (int)cudaGetLastError();
+  shape_of<N, EQ>(variant, epb, &threads, &smem);
+  // an error left by an earlier call is not this launch's: report it as such
+  const cudaError_t stale = cudaGetLastError();
+  if (stale != cudaSuccess) return (int)stale;
+  if (variant == kNodeKernel)
+    stage_kernel_np<NDG_DIM, N, EQ, NDG_REAL><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
+  else
+    stage_kernel<NDG_DIM, N, EQ, NDG_REAL><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFuncAttributes fa{};
+    if (variant == kNodeKernel) cudaFuncGetAttributes(&fa, stage_kernel_np<NDG_DIM, N, EQ, NDG_REAL>);
+    else cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL>);
+    launch_error_detail(grid, threads, smem, fa.maxThreadsPerBlock, fa.numRegs, fa.localSizeBytes,
+                        fa.maxDynamicSharedSizeBytes);
+  }
+  return (int)e;
 }
 
-template <int N, int EQ>
-int prepare_one(int epb, int* max_blocks) {
-  int threads;
-  size_t smem;
-  stage_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, &threads, &smem);
-  auto fn = stage_kernel<NDG_DIM, N, EQ, NDG_REAL>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename F>
+int occupancy(F fn, int threads, size_t smem, int* max_blocks) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return (int)e;
+  if (threads > fa.maxThreadsPerBlock) return (int)cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   int nb = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
@@ -64,8 +89,18 @@ int prepare_one(int epb, int* max_blocks) {
 }
 
 template <int N, int EQ>
-void shape_one(int epb, int* threads, size_t* smem) {
-  stage_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, threads, smem);
+int prepare_one(int variant, int epb, int* max_blocks) {
+  int threads;
+  size_t smem;
+  shape_of<N, EQ>(variant, epb, &threads, &smem);
+  if (threads > 1024 || threads < 1) return (int)cudaErrorInvalidConfiguration;
+  if (variant == kNodeKernel) return occupancy(stage_kernel_np<NDG_DIM, N, EQ, NDG_REAL>, threads, smem, max_blocks);
+  return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL>, threads, smem, max_blocks);
+}
+
+template <int N, int EQ>
+void shape_one(int variant, int epb, int* threads, size_t* smem) {
+  shape_of<N, EQ>(variant, epb, threads, smem);
 }
 
 }  // namespace
@@ -84,9 +119,9 @@ void shape_one(int epb, int* threads, size_t* smem) {
     default: break;                                              \
   }
 
-using LaunchFn = int (*)(int, int, const SolveDesc*, const GroupHeader*, const StagePlan&, void*);
-using PrepareFn = int (*)(int, int*);
-using ShapeFn = void (*)(int, int*, size_t*);
+using LaunchFn = int (*)(int, int, int, const SolveDesc*, const GroupHeader*, const StagePlan&, void*);
+using PrepareFn = int (*)(int, int, int*);
+using ShapeFn = void (*)(int, int, int*, size_t*);
 
 LaunchFn NDG_CAT(NDG_TAG, _launch)(int degree, int equation) { NDG_SWITCH(&launch_one) return nullptr; }
 PrepareFn NDG_CAT(NDG_TAG, _prepare)(int degree, int equation) { NDG_SWITCH(&prepare_one) return nullptr; }

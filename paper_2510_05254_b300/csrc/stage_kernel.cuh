@@ -36,6 +36,7 @@ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 // constant bank, so the contraction's coefficients are constant operands).
 template <typename real>
 struct BasisArgs {
+  real D[64];    // D[i*n + m] (the node-per-thread kernel)
   real Ae[16];   // [i*4 + m], i, m < n/2
   real Bo[16];
   real Cmid[4];  // D[i][mid], odd n
@@ -49,6 +50,97 @@ struct StageArgs {
   StagePlan plan;
   BasisArgs<real> basis;
 };
+
+// Per-solve coefficients in the kernel's precision (no conversion in device code).
+template <typename real> struct Coef;
+template <> struct Coef<double> {
+  __device__ static double vol(const SolveDesc* s, int a) { return s->vol_scale[a]; }
+  __device__ static double lo(const SolveDesc* s, int a) { return s->lift_lo[a]; }
+  __device__ static double hi(const SolveDesc* s, int a) { return s->lift_hi[a]; }
+  __device__ static double c(const SolveDesc* s) { return s->c; }
+  __device__ static double c2(const SolveDesc* s) { return s->c2; }
+};
+template <> struct Coef<float> {
+  __device__ static float vol(const SolveDesc* s, int a) { return s->f_vol_scale[a]; }
+  __device__ static float lo(const SolveDesc* s, int a) { return s->f_lift_lo[a]; }
+  __device__ static float hi(const SolveDesc* s, int a) { return s->f_lift_hi[a]; }
+  __device__ static float c(const SolveDesc* s) { return s->f_c; }
+  __device__ static float c2(const SolveDesc* s) { return s->f_c2; }
+};
+
+// The fields of the solve a tile belongs to, kept in registers while consecutive tiles of a CTA
+// belong to the same solve (always, for a single-solve launch): re-reading the descriptor per
+// tile costs a dozen loads per thread, which the node-per-thread kernel would pay per node.
+template <int DIM, typename real>
+struct SolveRegs {
+  int index = -1;
+  int tile_begin;
+  long long nelem;
+  unsigned E0, E1, E2;
+  const real* uin;
+  const real* un;
+  real* acc;
+  real* uout;
+  real* kw;
+  real vs[DIM], qlo[DIM], qhi[DIM];
+  real c, c2;
+  real a_self, bdt, dts;  // a_self * dt', b * dt', dt' = dt * rhs_scale
+
+  __device__ __forceinline__ void load(const SolveDesc* sd, int i, const StagePlan& plan) {
+    index = i;
+    tile_begin = sd->tile_begin;
+    nelem = sd->nelem;
+    E0 = (unsigned)sd->E[0];
+    E1 = (unsigned)sd->E[1];
+    E2 = (unsigned)sd->E[2];
+    uin = static_cast<const real*>(sd->buf[plan.in]);
+    un = static_cast<const real*>(sd->buf[kUN]);
+    acc = static_cast<real*>(sd->buf[kACC]);
+    uout = static_cast<real*>(sd->buf[plan.out]);
+    kw = plan.kwrite >= 0 ? static_cast<real*>(sd->buf[plan.kwrite]) : nullptr;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      vs[a] = Coef<real>::vol(sd, a);
+      qlo[a] = Coef<real>::lo(sd, a);
+      qhi[a] = Coef<real>::hi(sd, a);
+    }
+    c = Coef<real>::c(sd);
+    c2 = Coef<real>::c2(sd);
+    const double dt = sd->dt * sd->rhs_scale;  // the kernels hold L(U) / rhs_scale
+    a_self = (real)(plan.a_self * dt);
+    bdt = (real)(plan.b * dt);
+    dts = (real)dt;
+  }
+  // coefficient of stored slope j in the stage combination (RK6)
+  __device__ __forceinline__ real a_read(const StagePlan& plan, int j) const {
+    if constexpr (sizeof(real) == 4) return plan.a_read_f[j] * dts;
+    else return plan.a_read[j] * dts;
+  }
+};
+
+// Index of the solve owning `tile` (binary search over tile_begin; none for one solve).
+__device__ __forceinline__ int find_solve(const SolveDesc* solves, int nsolves, int tile) {
+  int lo = 0, hi = nsolves - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (solves[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Asynchronous global -> shared copy of one element (cp.async, no register round trip); many
+// can be in flight per thread.  Completed by cp_async_wait_all().
+template <typename real>
+__device__ __forceinline__ void cp_async_elem(real* smem_dst, const real* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(real) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 template <int N, typename real>
 __device__ __forceinline__ void contract_even_odd(const real (&f)[N + 1], real (&out)[N + 1],
@@ -90,6 +182,7 @@ struct StageGeom {
   static constexpr int NV = EQ == 0 ? 1 : DIM + 1;  // variables
   static constexpr int SPE = (n + 1) * L;           // padded shared slots per element
   static constexpr int NS = EQ == 0 ? 2 * NV : 2 * NV + DIM;  // shared arrays of SPE per element
+  static constexpr int NB = 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   __device__ static __forceinline__ int pad(int node) { return node + node / n; }
 };
 
@@ -103,25 +196,27 @@ __global__ void stage_kernel(const StageArgs<real> args) {
   real* sU = reinterpret_cast<real*>(smem_raw);  // [NV][epb][SPE]
   real* sR = sU + NV * epb * SPE;                 // [NV][epb][SPE]
   real* sV = sR + NV * epb * SPE;                 // [DIM][epb][SPE] (Euler)
+  real* sB = sU + G::NS * epb * SPE;              // [NV][epb][NPE]: U^n of the tile (stage update)
+  real* sA = sB + NV * epb * NPE;                 // [NV][epb][NPE]: ACC of the tile
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
   const StagePlan& plan = args.plan;
 
+  SolveRegs<DIM, real> S;
   for (int tile = blockIdx.x; tile < hdr.ntiles; tile += gridDim.x) {
-    // ---- which solve owns this tile (binary search over tile_begin) ----
-    int lo = 0, hi = hdr.nsolves - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (args.solves[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
-    }
-    const SolveDesc* sd = args.solves + lo;
-    const long long nelem = sd->nelem;
-    const long long e0 = (long long)(tile - sd->tile_begin) * epb;
+    // ---- which solve owns this tile; its fields stay in registers while it does not change ----
+    const int si = hdr.nsolves > 1 ? find_solve(args.solves, hdr.nsolves, tile) : 0;
+    if (si != S.index) S.load(args.solves + si, si, plan);
+    const long long nelem = S.nelem;
+    const long long e0 = (long long)(tile - S.tile_begin) * epb;
     const int cnt = (int)min((long long)epb, nelem - e0);
     const long long vstride = nelem * NPE;  // elements of one variable
-    const real* __restrict__ uin = static_cast<const real*>(sd->buf[plan.in]);
+    const real* __restrict__ uin = S.uin;
 
-    // ---- 1. tile of the stage input into shared memory ----
+    // ---- 1. the tile of the stage input, and U^n / ACC when the update reads them, copied into
+    //         shared memory asynchronously: every copy of the tile is in flight before the wait ----
+    const bool need_un = plan.in != kUN && plan.acc_mode != 3;
+    const bool need_acc = plan.acc_mode >= 2;
     {
       const int total = cnt * NPE;
 #pragma unroll
@@ -130,10 +225,21 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         real* dst = sU + v * epb * SPE;
         for (int idx = tid; idx < total; idx += nthr) {
           const int el = idx / NPE, node = idx - el * NPE;
-          dst[el * SPE + G::pad(node)] = src[idx];
+          cp_async_elem(dst + el * SPE + G::pad(node), src + idx);
+        }
+        if (need_un) {
+          const real* s2 = S.un + v * vstride + e0 * NPE;
+          real* d2 = sB + v * epb * NPE;
+          for (int idx = tid; idx < total; idx += nthr) cp_async_elem(d2 + idx, s2 + idx);
+        }
+        if (need_acc) {
+          const real* s3 = S.acc + v * vstride + e0 * NPE;
+          real* d3 = sA + v * epb * NPE;
+          for (int idx = tid; idx < total; idx += nthr) cp_async_elem(d3 + idx, s3 + idx);
         }
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     // ---- 2. velocities (Euler) ----
     if constexpr (EQ == 1) {
@@ -148,7 +254,6 @@ __global__ void stage_kernel(const StageArgs<real> args) {
       __syncthreads();
     }
     // ---- 3. volume + surface terms, axis by axis ----
-    const int E0 = sd->E[0], E1 = sd->E[1];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const int el = tid / L;
@@ -164,35 +269,36 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         } else {
           pbase = line % n + (n + 1) * (line / n); pstride = (n + 1) * n; ubase = line; ustride = n * n;
         }
-        // periodic neighbours along axis a
-        const long long e = e0 + el;
+        // periodic neighbours along axis a (element indices fit in 32 bits, checked at creation)
         long long elo, ehi;
         {
-          const long long ex = e % E0;
-          const long long rest = e / E0;
+          const unsigned eu = (unsigned)(e0 + el);
+          const unsigned U0 = S.E0, U1 = S.E1;
+          unsigned lo_, hi_;
           if (a == 0) {
-            elo = e - ex + (ex == 0 ? E0 - 1 : ex - 1);
-            ehi = e - ex + (ex == E0 - 1 ? 0 : ex + 1);
+            const unsigned ex = eu % U0;
+            lo_ = eu - ex + (ex == 0 ? U0 - 1 : ex - 1);
+            hi_ = eu - ex + (ex == U0 - 1 ? 0 : ex + 1);
           } else if (a == 1) {
-            const long long ey = rest % E1;
-            const long long step = E0;
-            elo = e + (ey == 0 ? (long long)(E1 - 1) * step : -step);
-            ehi = e + (ey == E1 - 1 ? -(long long)(E1 - 1) * step : step);
+            const unsigned ey = (eu / U0) % U1;
+            lo_ = ey == 0 ? eu + (U1 - 1) * U0 : eu - U0;
+            hi_ = ey == U1 - 1 ? eu - (U1 - 1) * U0 : eu + U0;
           } else {
-            const long long ez = rest / E1;
-            const long long E2 = sd->E[2];
-            const long long step = (long long)E0 * E1;
-            elo = e + (ez == 0 ? (E2 - 1) * step : -step);
-            ehi = e + (ez == E2 - 1 ? -(E2 - 1) * step : step);
+            const unsigned step = U0 * U1, U2 = S.E2;
+            const unsigned ez = eu / step;
+            lo_ = ez == 0 ? eu + (U2 - 1) * step : eu - step;
+            hi_ = ez == U2 - 1 ? eu - (U2 - 1) * step : eu + step;
           }
+          elo = lo_;
+          ehi = hi_;
         }
         const bool lo_in = elo >= e0 && elo < e0 + cnt;
         const bool hi_in = ehi >= e0 && ehi < e0 + cnt;
         const real* sUe = sU + el * SPE + pbase;
         real* sRe = sR + el * SPE + pbase;
-        const real vs = (real)sd->vol_scale[a];
-        const real qlo = (real)sd->lift_lo[a];
-        const real qhi = (real)sd->lift_hi[a];
+        const real vs = S.vs[a];
+        const real qlo = S.qlo[a];
+        const real qhi = S.qhi[a];
         // vs is exactly 1 on axis 0 unless the advection velocity has no x component
         const bool unit = (a == 0) && vs == real(1);
         if constexpr (EQ == 0) {
@@ -224,8 +330,8 @@ __global__ void stage_kernel(const StageArgs<real> args) {
                            : uin[v * vstride + ehi * NPE + ubase];
           }
           const real* sVa = sV + a * epb * SPE + el * SPE + pbase;
-          const real c2 = (real)sd->c2;
-          const real cs = (real)sd->c;
+          const real c2 = S.c2;
+          const real cs = S.c;
           // normal velocities and LLF alpha at both faces of the line
           const real un0 = sVa[0], unN = sVa[N * pstride];
           const real unlo = xlo[1 + a] / xlo[0];
@@ -280,18 +386,18 @@ __global__ void stage_kernel(const StageArgs<real> args) {
     }
     // ---- 4. Runge-Kutta stage update ----
     {
-      const double dt = sd->dt * sd->rhs_scale;  // shared memory holds L(U) / rhs_scale
-      const real a_self = (real)(plan.a_self * dt);
-      const real bdt = (real)(plan.b * dt);
-      real* __restrict__ uout = static_cast<real*>(sd->buf[plan.out]);
-      real* __restrict__ acc = static_cast<real*>(sd->buf[kACC]);
-      const real* __restrict__ un = static_cast<const real*>(sd->buf[kUN]);
-      real* __restrict__ kw = plan.kwrite >= 0 ? static_cast<real*>(sd->buf[plan.kwrite]) : nullptr;
+      const real a_self = S.a_self;
+      const real bdt = S.bdt;
+      real* __restrict__ uout = S.uout;
+      real* __restrict__ acc = S.acc;
+      real* __restrict__ kw = S.kw;
       const int total = cnt * NPE;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const real* sRv = sR + v * epb * SPE;
         const real* sUv = sU + v * epb * SPE;
+        const real* sBv = sB + v * epb * NPE;
+        const real* sAv = sA + v * epb * NPE;
         const long long goff = v * vstride + e0 * NPE;
         for (int idx = tid; idx < total; idx += nthr) {
           const int el = idx / NPE, node = idx - el * NPE;
@@ -299,18 +405,18 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           const long long g = goff + idx;
           const real r = sRv[s];
           if (plan.acc_mode == 3) {
-            uout[g] = fma(bdt, r, acc[g]);
+            uout[g] = fma(bdt, r, sAv[idx]);
             continue;
           }
-          const real base = plan.in == kUN ? sUv[s] : un[g];
+          const real base = plan.in == kUN ? sUv[s] : sBv[idx];
           real o = fma(a_self, r, base);
           for (int j = 0; j < plan.nread; ++j) {
-            const real* kj = static_cast<const real*>(sd->buf[plan.kread[j]]);
-            o = fma((real)(plan.a_read[j] * dt), kj[g], o);
+            const real* kj = static_cast<const real*>(args.solves[si].buf[plan.kread[j]]);
+            o = fma(S.a_read(plan, j), kj[g], o);
           }
           uout[g] = o;
           if (plan.acc_mode == 1) acc[g] = fma(bdt, r, base);
-          else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, acc[g]);
+          else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, sAv[idx]);
           if (kw) kw[g] = r;  // the slope L(U_in) / rhs_scale; the combination applies a*dt*rhs_scale
         }
       }
@@ -323,7 +429,7 @@ template <int DIM, int N, int EQ, typename real>
 void stage_shape(int epb, int* threads, size_t* smem) {
   using G = StageGeom<DIM, N, EQ, real>;
   *threads = epb * G::L;
-  *smem = (size_t)G::NS * epb * G::SPE * sizeof(real);
+  *smem = ((size_t)G::NS * G::SPE + (size_t)G::NB * G::NPE) * epb * sizeof(real);
 }
 
 }  // namespace ndg

@@ -20,6 +20,7 @@ NDG_FLUX_UPWIND, NDG_FLUX_LLF = 0, 1
 NDG_RK3, NDG_RK4, NDG_RK6 = 3, 4, 6
 NDG_F64, NDG_F32 = 0, 1
 NDG_LAYOUT_ELEMENT, NDG_LAYOUT_GRID = 0, 1
+NDG_KERNEL_AUTO, NDG_KERNEL_LINE, NDG_KERNEL_NODE = 0, 1, 2
 STATUS_NAMES = {0: "NDG_OK", 1: "NDG_EINVAL", 2: "NDG_ENOMEM", 3: "NDG_ECUDA", 4: "NDG_ENONFINITE",
                 5: "NDG_EAGAIN", 6: "NDG_ETIMEOUT", 7: "NDG_ESTATE"}
 
@@ -35,7 +36,7 @@ class ndg_config(ctypes.Structure):
                 ("equation", ctypes.c_int), ("flux", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("length", ctypes.c_double * 3), ("velocity", ctypes.c_double * 3),
                 ("sound_speed", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("elems_per_block", ctypes.c_int), ("device", ctypes.c_int)]
+                ("elems_per_block", ctypes.c_int), ("device", ctypes.c_int), ("kernel", ctypes.c_int)]
 
 
 class ndg_norms_t(ctypes.Structure):
@@ -47,7 +48,7 @@ class ndg_norms_t(ctypes.Structure):
 class ndg_info_t(ctypes.Structure):
     _fields_ = [("nvar", ctypes.c_int), ("nodes_per_elem", ctypes.c_int), ("nelem", ctypes.c_int64),
                 ("ndof", ctypes.c_int64), ("state_bytes", ctypes.c_size_t),
-                ("device_bytes", ctypes.c_size_t), ("elems_per_block", ctypes.c_int)]
+                ("device_bytes", ctypes.c_size_t), ("elems_per_block", ctypes.c_int), ("kernel", ctypes.c_int)]
 
 
 class ndg_solve_stats_t(ctypes.Structure):

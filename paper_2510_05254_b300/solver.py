@@ -19,7 +19,7 @@ class Solver:
     def __init__(self, dim: int, degree: int, elems, equation: int = nat.NDG_ADVECTION,
                  flux: int | None = None, dtype: str = "f64", length=(1.0, 1.0, 1.0),
                  velocity=(1.0, 0.0, 0.0), sound_speed: float = 1.0, elems_per_block: int = 0,
-                 device: int = 0, stream: torch.cuda.Stream | None = None):
+                 device: int = 0, stream: torch.cuda.Stream | None = None, kernel: int = 0):
         if flux is None:
             flux = nat.NDG_FLUX_UPWIND if equation == nat.NDG_ADVECTION else nat.NDG_FLUX_LLF
         self.dtype_code, self.torch_dtype, self.np_dtype = DTYPES[dtype]
@@ -37,12 +37,14 @@ class Solver:
         cfg.stream = self.stream.cuda_stream
         cfg.elems_per_block = elems_per_block
         cfg.device = device
+        cfg.kernel = kernel
         self.cfg = cfg
         self.dim, self.degree = dim, degree
         self.ctx = nat.ndg_create_ex(cfg)
         info = nat.ndg_info(self.ctx)
         self.nvar, self.npe, self.nelem = info.nvar, info.nodes_per_elem, info.nelem
         self.ndof, self.state_bytes = info.ndof, info.state_bytes
+        self.kernel = info.kernel
         self.shape = (self.nvar, self.nelem, self.npe)
 
     # ---- state ----
@@ -91,7 +93,10 @@ class Solver:
         return X
 
     def autotune(self, rk: int = nat.NDG_RK4):
-        return nat.ndg_autotune(self.ctx, rk)
+        """(elements per block, ms per step) of the best tile; the mapping is in self.kernel."""
+        best = nat.ndg_autotune(self.ctx, rk)
+        self.kernel = nat.ndg_info(self.ctx).kernel
+        return best
 
     def synchronize(self) -> None:
         nat.ndg_synchronize(self.ctx)
