@@ -51,12 +51,12 @@ enum { NDG_FLUX_UPWIND = 0, NDG_FLUX_LLF = 1 };  /* Eq. (LF); upwind is valid fo
 enum { NDG_RK3 = 3, NDG_RK4 = 4, NDG_RK6 = 6 };  /* Eq. (RK3), Eq. (RK4), Eq. (RK6) */
 enum { NDG_F64 = 0, NDG_F32 = 1 };               /* state/arithmetic precision on the GPU */
 enum { NDG_LAYOUT_ELEMENT = 0, NDG_LAYOUT_GRID = 1 };
-/* Thread mapping of the stage kernel.  LINE = one thread per line of nodes, D applied through
- * its even-odd halves (fewest FP64 operations); NODE = one thread per node, plain n-term sums,
- * right-hand side in registers (fewest memory round trips).  The two round differently (both
- * are within the parity tolerances); for a given mapping results do not depend on the tile size.
- * AUTO = the autotuned choice for the kernel class, else LINE for FP64 and NODE for FP32. */
-enum { NDG_KERNEL_AUTO = 0, NDG_KERNEL_LINE = 1, NDG_KERNEL_NODE = 2 };
+/* Thread mapping of the stage kernel (identical arithmetic, bitwise-identical results):
+ * LINE = one thread per line of nodes for all variables (fewest FP64 operations),
+ * LINE_VAR = one thread per (line, variable): nvar times more threads per element for the same
+ * shared memory (higher occupancy for isothermal Euler).
+ * AUTO = the autotuned choice for the kernel class, else LINE. */
+enum { NDG_KERNEL_AUTO = 0, NDG_KERNEL_LINE = 1, NDG_KERNEL_LINE_VAR = 2 };
 
 typedef struct ndg_ctx ndg_ctx;     /* one solve: state, buffers, stream, launch plan */
 typedef struct ndg_batch ndg_batch; /* several solves stepped by one graph per RK step */
@@ -76,7 +76,7 @@ typedef struct {
   void* stream;       /* cudaStream_t to run on; NULL: the context creates its own */
   int elems_per_block;/* elements per CTA of the stage kernel; 0: library default */
   int device;         /* CUDA device ordinal; default 0 */
-  int kernel;         /* NDG_KERNEL_AUTO (default), NDG_KERNEL_LINE or NDG_KERNEL_NODE */
+  int kernel;         /* NDG_KERNEL_AUTO (default), NDG_KERNEL_LINE or NDG_KERNEL_LINE_VAR */
 } ndg_config;
 
 /* Norms by LGL quadrature on every element (Sec. 3.1's L2 norm). */
@@ -98,7 +98,7 @@ typedef struct {
   size_t state_bytes;  /* ndof * sizeof(real) */
   size_t device_bytes; /* device memory the context holds now */
   int elems_per_block; /* stage-kernel tile in use */
-  int kernel;          /* stage-kernel mapping in use: NDG_KERNEL_LINE or NDG_KERNEL_NODE */
+  int kernel;          /* stage-kernel mapping in use: NDG_KERNEL_LINE or NDG_KERNEL_LINE_VAR */
 } ndg_info_t;
 
 /* Fill cfg with defaults: 2D, degree 7, 16x16 elements, advection, upwind, FP64, unit square,

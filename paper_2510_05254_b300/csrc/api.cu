@@ -283,15 +283,11 @@ int num_sms(int device) {
 
 int default_epb_for(const KernelClass& kc, int variant) {
   const int n = kc.degree + 1;
-  if (variant == kNodeKernel) {  // node-per-thread kernel: about 256 threads per CTA
-    int npe = 1;
-    for (int d = 0; d < kc.dim; ++d) npe *= n;
-    return std::max(1, 256 / npe);
-  }
-  // line-per-thread kernel: about 128-256 threads per CTA (lines per element = n^(dim-1)), and
-  // at most ~100 KB of shared memory so that two CTAs fit on an SM
+  // about 128-256 threads per CTA (threads per element = n^(dim-1), times nvar for the
+  // (line, variable) mapping), and at most ~100 KB of shared memory so that two CTAs fit on an SM
   int L = 1;
   for (int d = 1; d < kc.dim; ++d) L *= n;
+  if (variant == kLineVarKernel) L *= kc.equation == NDG_ADVECTION ? 1 : kc.dim + 1;
   int epb = std::max(1, 256 / L);
   if (kc.dim == 3) epb = std::max(1, 192 / L);
   epb = std::min(epb, 64);
@@ -305,11 +301,11 @@ int default_epb_for(const KernelClass& kc, int variant) {
   return epb;
 }
 
-// Untuned choice: the line kernel (fewest FP64 operations) for FP64, the node kernel (fewest
-// memory round trips) for FP32.
+// Untuned choice: one thread per line (measured faster on B300 than one thread per line and
+// variable for every class tried; the autotuner still tries both).
 TileConfig default_tile(const KernelClass& kc) {
   TileConfig t;
-  t.variant = kc.dtype == NDG_F32 ? kNodeKernel : kLineKernel;
+  t.variant = kLineKernel;
   t.epb = default_epb_for(kc, t.variant);
   return t;
 }
@@ -332,7 +328,7 @@ void load_tune_cache_locked() {
   if (!f) return;
   int d, n, e, t, epb, var;
   while (std::fscanf(f, "%d %d %d %d %d %d", &d, &n, &e, &t, &epb, &var) == 6)
-    if (epb > 0 && epb <= 1024 && (var == kLineKernel || var == kNodeKernel))
+    if (epb > 0 && epb <= 1024 && (var == kLineKernel || var == kLineVarKernel))
       g_tuned.emplace(class_key(KernelClass{d, n, e, t}), TileConfig{epb, var});
   std::fclose(f);
 }
@@ -537,7 +533,7 @@ int check_config(const ndg_config& k) {
   if (k.equation == NDG_ISO_EULER && !(k.sound_speed > 0.0 && std::isfinite(k.sound_speed)))
     return fail(NDG_EINVAL, "sound speed must be positive");
   if (k.elems_per_block < 0) return fail(NDG_EINVAL, "elems_per_block must be >= 0");
-  if (k.kernel != NDG_KERNEL_AUTO && k.kernel != NDG_KERNEL_LINE && k.kernel != NDG_KERNEL_NODE)
+  if (k.kernel != NDG_KERNEL_AUTO && k.kernel != NDG_KERNEL_LINE && k.kernel != NDG_KERNEL_LINE_VAR)
     return fail(NDG_EINVAL, "unknown kernel mapping %d", k.kernel);
   return NDG_OK;
 }
@@ -657,7 +653,7 @@ int ndg_create_ex(const ndg_config* cfg, ndg_ctx** out) {
     TileConfig t = tuned_tile(c->kc);
     if (!t.epb) t = default_tile(c->kc);
     if (k.kernel == NDG_KERNEL_LINE) t.variant = kLineKernel;
-    if (k.kernel == NDG_KERNEL_NODE) t.variant = kNodeKernel;
+    if (k.kernel == NDG_KERNEL_LINE_VAR) t.variant = kLineVarKernel;
     if (k.kernel != NDG_KERNEL_AUTO && !k.elems_per_block) t.epb = default_epb_for(c->kc, t.variant);
     if (k.elems_per_block) t.epb = k.elems_per_block;
     t.epb = (int)std::min<long long>(t.epb, nelem);
@@ -694,7 +690,7 @@ int ndg_info(const ndg_ctx* c, ndg_info_t* o) {
   o->state_bytes = c->state_bytes;
   o->device_bytes = c->device_bytes;
   o->elems_per_block = c->tile.epb;
-  o->kernel = c->tile.variant == kNodeKernel ? NDG_KERNEL_NODE : NDG_KERNEL_LINE;
+  o->kernel = c->tile.variant == kLineVarKernel ? NDG_KERNEL_LINE_VAR : NDG_KERNEL_LINE;
   return NDG_OK;
 }
 
@@ -918,9 +914,10 @@ int ndg_autotune(ndg_ctx* c, int rk, int* best_epb, double* best_ms) {
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   const TileConfig orig = c->tile;
-  for (int variant : {kLineKernel, kNodeKernel}) {
+  for (int variant : {kLineKernel, kLineVarKernel}) {
     if (c->cfg.kernel == NDG_KERNEL_LINE && variant != kLineKernel) continue;
-    if (c->cfg.kernel == NDG_KERNEL_NODE && variant != kNodeKernel) continue;
+    if (c->cfg.kernel == NDG_KERNEL_LINE_VAR && variant != kLineVarKernel) continue;
+    if (variant == kLineVarKernel && c->nvar == 1) continue;  // same kernel as kLineKernel
     for (int epb : cands) {
       if (epb > c->nelem) break;
       int threads;

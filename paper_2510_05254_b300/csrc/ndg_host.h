@@ -26,7 +26,7 @@ bool valid_rk(int rk);
 // Launch resources of one kernel class over a set of solves (one persistent launch per stage).
 struct Group {
   KernelClass kc{};
-  int variant = 0;  // kLineKernel / kNodeKernel
+  int variant = 0;  // kLineKernel / kLineVarKernel
   int epb = 0;
   int grid = 0;
   int ntiles = 0;

@@ -71,13 +71,14 @@ struct GroupHeader {
   int nsolves;
   int ntiles;
   int epb;                // elements per CTA tile
-  int variant;            // kernel mapping: kLineKernel or kNodeKernel
+  int variant;            // kernel mapping: kLineKernel or kLineVarKernel
 };
 
-// Kernel mappings of one stage (same arithmetic per element, different thread mapping):
-// kLineKernel: one thread per line of n nodes, even-odd D (fewest FP64 operations);
-// kNodeKernel: one thread per node, right-hand side in registers (fewest memory round trips).
-enum { kLineKernel = 0, kNodeKernel = 1 };
+// Thread mappings of one stage (identical arithmetic, bitwise-identical results):
+// kLineKernel: one thread per line of n nodes for all variables (fewest FP64 operations);
+// kLineVarKernel: one thread per (line, variable): more threads per element for the same
+// shared memory (higher occupancy for the multi-variable Euler classes).
+enum { kLineKernel = 0, kLineVarKernel = 1 };
 
 // Kernel class: everything that is a template parameter of the stage kernel.
 struct KernelClass {

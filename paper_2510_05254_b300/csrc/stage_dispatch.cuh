@@ -5,7 +5,6 @@
 #include <type_traits>
 
 #include "stage_kernel.cuh"
-#include "stage_np_kernel.cuh"
 
 namespace ndg {
 
@@ -22,7 +21,6 @@ const BasisArgs<real>& basis_args(int N) {
       BasisArgs<real>& t = table[d];
       std::memset(&t, 0, sizeof(t));
       const int n = d + 1, h = n / 2;
-      for (int i = 0; i < n * n; ++i) t.D[i] = (real)b.D[i];
       for (int i = 0; i < h; ++i)
         for (int m = 0; m < h; ++m) {
           t.Ae[i * 4 + m] = (real)b.Ae[i * kMaxN + m];
@@ -37,12 +35,17 @@ const BasisArgs<real>& basis_args(int N) {
   return table[N];
 }
 
-// Two thread mappings of the same stage (see kLineKernel / kNodeKernel); the tile autotuner
+// Two thread mappings of the same stage (see kLineKernel / kLineVarKernel); the tile autotuner
 // picks one per kernel class.
 template <int N, int EQ>
 void shape_of(int variant, int epb, int* threads, size_t* smem) {
-  if (variant == kNodeKernel) stage_np_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, threads, smem);
-  else stage_shape<NDG_DIM, N, EQ, NDG_REAL>(epb, threads, smem);
+  if (variant == kLineVarKernel) stage_shape<NDG_DIM, N, EQ, NDG_REAL, true>(epb, threads, smem);
+  else stage_shape<NDG_DIM, N, EQ, NDG_REAL, false>(epb, threads, smem);
+}
+
+template <int N, int EQ, bool VS>
+void launch_kernel(int grid, int threads, size_t smem, void* stream, const StageArgs<NDG_REAL>& args) {
+  stage_kernel<NDG_DIM, N, EQ, NDG_REAL, VS><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
 }
 
 template <int N, int EQ>
@@ -59,15 +62,13 @@ int launch_one(int variant, int grid, int epb, const SolveDesc* solves, const Gr
   // an error left by an earlier call is not this launch's: report it as such
   const cudaError_t stale = cudaGetLastError();
   if (stale != cudaSuccess) return (int)stale;
-  if (variant == kNodeKernel)
-    stage_kernel_np<NDG_DIM, N, EQ, NDG_REAL><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
-  else
-    stage_kernel<NDG_DIM, N, EQ, NDG_REAL><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
+  if (variant == kLineVarKernel) launch_kernel<N, EQ, true>(grid, threads, smem, stream, args);
+  else launch_kernel<N, EQ, false>(grid, threads, smem, stream, args);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaFuncAttributes fa{};
-    if (variant == kNodeKernel) cudaFuncGetAttributes(&fa, stage_kernel_np<NDG_DIM, N, EQ, NDG_REAL>);
-    else cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL>);
+    if (variant == kLineVarKernel) cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL, true>);
+    else cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL, false>);
     launch_error_detail(grid, threads, smem, fa.maxThreadsPerBlock, fa.numRegs, fa.localSizeBytes,
                         fa.maxDynamicSharedSizeBytes);
   }
@@ -94,8 +95,9 @@ int prepare_one(int variant, int epb, int* max_blocks) {
   size_t smem;
   shape_of<N, EQ>(variant, epb, &threads, &smem);
   if (threads > 1024 || threads < 1) return (int)cudaErrorInvalidConfiguration;
-  if (variant == kNodeKernel) return occupancy(stage_kernel_np<NDG_DIM, N, EQ, NDG_REAL>, threads, smem, max_blocks);
-  return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL>, threads, smem, max_blocks);
+  if (variant == kLineVarKernel)
+    return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL, true>, threads, smem, max_blocks);
+  return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL, false>, threads, smem, max_blocks);
 }
 
 template <int N, int EQ>

@@ -36,7 +36,6 @@ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 // constant bank, so the contraction's coefficients are constant operands).
 template <typename real>
 struct BasisArgs {
-  real D[64];    // D[i*n + m] (the node-per-thread kernel)
   real Ae[16];   // [i*4 + m], i, m < n/2
   real Bo[16];
   real Cmid[4];  // D[i][mid], odd n
@@ -70,7 +69,7 @@ template <> struct Coef<float> {
 
 // The fields of the solve a tile belongs to, kept in registers while consecutive tiles of a CTA
 // belong to the same solve (always, for a single-solve launch): re-reading the descriptor per
-// tile costs a dozen loads per thread, which the node-per-thread kernel would pay per node.
+// tile costs a dozen loads per thread and tile.
 template <int DIM, typename real>
 struct SolveRegs {
   int index = -1;
@@ -174,7 +173,7 @@ __device__ __forceinline__ void contract_even_odd(const real (&f)[N + 1], real (
   }
 }
 
-template <int DIM, int N, int EQ, typename real>
+template <int DIM, int N, int EQ, typename real, bool VS = false>
 struct StageGeom {
   static constexpr int n = N + 1;
   static constexpr int L = ipow_c(n, DIM - 1);      // lines per element along one axis
@@ -183,13 +182,19 @@ struct StageGeom {
   static constexpr int SPE = (n + 1) * L;           // padded shared slots per element
   static constexpr int NS = EQ == 0 ? 2 * NV : 2 * NV + DIM;  // shared arrays of SPE per element
   static constexpr int NB = 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
+  // threads per element: one per line, or (VS) one per line and variable
+  static constexpr int TPE = VS ? L * NV : L;
   __device__ static __forceinline__ int pad(int node) { return node + node / n; }
 };
 
-template <int DIM, int N, int EQ, typename real>
+// VS = false: a thread owns a line for every variable (fewest FP64 operations: the wave speeds
+// of the face flux are computed once per line).  VS = true: a thread owns one (line, variable)
+// pair, so an Euler CTA has nvar times more threads for the same shared memory; the operations
+// per variable are the same, in the same order, so the results are bitwise identical.
+template <int DIM, int N, int EQ, typename real, bool VS>
 __global__ void stage_kernel(const StageArgs<real> args) {
-  using G = StageGeom<DIM, N, EQ, real>;
-  constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE;
+  using G = StageGeom<DIM, N, EQ, real, VS>;
+  constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const GroupHeader hdr = *args.hdr;
   const int epb = hdr.epb;
@@ -256,8 +261,10 @@ __global__ void stage_kernel(const StageArgs<real> args) {
     // ---- 3. volume + surface terms, axis by axis ----
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      const int el = tid / L;
-      const int line = tid - el * L;
+      const int el = tid / TPE;
+      const int rem = tid - el * TPE;
+      const int line = rem % L;
+      const int vsel = rem / L;  // the variable this thread owns (VS), else 0
       if (el < cnt) {
         // padded base / stride in shared memory; unpadded base / stride in global memory
         int pbase, pstride, ubase, ustride;
@@ -340,6 +347,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           const real ahi = fmax(fabs(unN), fabs(unhi)) + cs;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
+            if (VS && v != vsel) continue;
             const real* sUv = sUe + v * epb * SPE;
             real f[n], out[n];
             // flux component v along a (Eq. (eulerIso2d)): v = 0: m_a; v = 1 + b: m_b u_a
@@ -425,10 +433,10 @@ __global__ void stage_kernel(const StageArgs<real> args) {
   }
 }
 
-template <int DIM, int N, int EQ, typename real>
+template <int DIM, int N, int EQ, typename real, bool VS>
 void stage_shape(int epb, int* threads, size_t* smem) {
-  using G = StageGeom<DIM, N, EQ, real>;
-  *threads = epb * G::L;
+  using G = StageGeom<DIM, N, EQ, real, VS>;
+  *threads = epb * G::TPE;
   *smem = ((size_t)G::NS * G::SPE + (size_t)G::NB * G::NPE) * epb * sizeof(real);
 }
 

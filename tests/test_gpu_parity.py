@@ -114,9 +114,9 @@ def test_oversized_tile_is_rejected():
     with pytest.raises(nat.NdgError) as ei:
         make(2, 7, (9, 8), 1, epb=64)
     assert ei.value.status == nat.NDG_EINVAL
-    # 3 elements of 216 nodes = 648 threads exceed the node kernel's 512-thread blocks
+    # 8 elements x 36 lines x 4 variables = 1152 threads exceed 1024
     with pytest.raises(nat.NdgError) as ei:
-        Solver(3, 5, (2, 2, 3), elems_per_block=3, kernel=nat.NDG_KERNEL_NODE, dtype="f32")
+        Solver(3, 5, (2, 2, 3), equation=1, elems_per_block=8, kernel=nat.NDG_KERNEL_LINE_VAR, dtype="f32")
     assert ei.value.status == nat.NDG_EINVAL
 
 
@@ -378,25 +378,30 @@ def test_torch_allocator_hook():
         nat.ndg_set_allocator(None, None)
 
 
-@pytest.mark.parametrize("kernel", [nat.NDG_KERNEL_LINE, nat.NDG_KERNEL_NODE])
+@pytest.mark.parametrize("kernel", [nat.NDG_KERNEL_LINE, nat.NDG_KERNEL_LINE_VAR])
 @pytest.mark.parametrize("dim,N,E,eq", [(1, 4, (7,), 1), (2, 7, (5, 3), 0), (2, 6, (4, 3), 1), (2, 3, (6, 5), 1),
                                         (3, 2, (3, 2, 3), 1), (3, 5, (2, 2, 3), 0), (3, 3, (2, 3, 2), 1)])
 def test_both_kernel_mappings(kernel, dim, N, E, eq):
-    """Line (even-odd) and node-per-thread mappings, FP64 within 1e-12 per step (RK4 and RK6),
-    FP32 within its tolerance, with tiles that leave a ragged end."""
+    """Thread per line (all variables) and thread per (line, variable): FP64 within 1e-12 per
+    step (RK4 and RK6), FP32 within its tolerance, with tiles that leave a ragged end; and the
+    two mappings agree bit for bit."""
     flux = 0 if eq == 0 else 1
     p = orc.Problem(dim=dim, degree=N, elems=E + (1,) * (3 - len(E)), equation=eq, flux=flux,
                     length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3))
     U = initial(p)
     dt = orc.stable_dt(p, U, 0.2)
+    kw = dict(equation=eq, flux=flux, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3))
     for rk in (4, 6):
-        s = Solver(dim, N, E, equation=eq, flux=flux, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3),
-                   elems_per_block=2, kernel=kernel)
+        s = Solver(dim, N, E, elems_per_block=2, kernel=kernel, **kw)
         assert s.kernel == kernel
         check(p, s, U, dt, 2, rk, F64_TOL)
-    s = Solver(dim, N, E, equation=eq, flux=flux, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3),
-               elems_per_block=2, kernel=kernel, dtype="f32")
-    s.set_state(U)
-    s.step(dt, 1, 4)
-    ref = orc.step(p, U.astype(np.float32).astype(np.float64), dt, 1, 4)
-    assert rel_l2(s.get_state(), ref) < F32_TOL
+    for dtype in ("f64", "f32"):
+        outs = []
+        for kern in (nat.NDG_KERNEL_LINE, nat.NDG_KERNEL_LINE_VAR):
+            s = Solver(dim, N, E, elems_per_block=2, kernel=kern, dtype=dtype, **kw)
+            s.set_state(U)
+            s.step(dt, 2, 4)
+            outs.append(s.get_state())
+        assert np.array_equal(outs[0], outs[1])
+    ref = orc.step(p, U.astype(np.float32).astype(np.float64), dt, 2, 4)
+    assert rel_l2(outs[1], ref) < 2 * F32_TOL
