@@ -105,7 +105,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], 0.0, set()
+        sm, mx, reasons, power = [], 0.0, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in getattr(self, "lines", []):
             f = [x.strip() for x in l.split(",")]
@@ -114,13 +114,17 @@ class ClockSampler:
                 mx = max(mx, float(f[2]))
             except (ValueError, IndexError):
                 continue
+            try:
+                power.append(float(f[3]))
+            except (ValueError, IndexError):
+                pass
             for name, val in zip(names, f[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w": statistics.median(power) if power else None}
 
 
 def dist_setup(args):
@@ -245,6 +249,7 @@ def run_solver_timed(dtype, args, dev, pg, U0_host):
     total_ms = start.elapsed_time(end)
     stage_ms = sum(a.elapsed_time(b) for a, b in inner) / (args.steps * NSTEPS * STAGES)
     out = {"total_ms": total_ms, "stage_ms": stage_ms, "ndof": s.ndof, "dt": dt, "clocks": clk.summary(), "epb": epb,
+           "kernel": "line" if s.kernel == 1 else "line_var",
            "l2_norm": nr.l2, "mass": nr.integral[0], "state_bytes": s.state_bytes}
     s.close()
     return out
@@ -290,15 +295,31 @@ def run_serving(args, dev):
     pool_stats, _ = serving.run_pool(reqs, math.inf, budget)
     torch.cuda.synchronize(dev)
     serial_stats, _ = serving.run_serial(reqs, math.inf)
+    # the one-solve-at-a-time FP64 path: every request in FP64, one after another
+    reqs64 = serving.prepare([dict(r, dtype="f64") for r in inputs.serving_stream(n, emax=args.serving_emax)],
+                             nsteps=100)
+    serial64_stats, _ = serving.run_serial(reqs64, math.inf)
+    del reqs64
     # latency at a finite arrival rate: half of the pool's measured capacity
     rate = 0.5 * pool_stats["solves_per_s"]
     pool_rate_stats, _ = serving.run_pool(reqs, rate, budget)
     return {"workload": f"{n} independent 2D solves (advection / isothermal Euler 50/50, elements per axis "
                         f"log-uniform in [16,{args.serving_emax}], degree in {{3,5,7}}, FP64/FP32 50/50), "
                         "100 RK4 steps each, 120 GB budget",
-            "burst": {"pool": pool_stats, "one_at_a_time": serial_stats,
-                      "speedup_solves_per_s": pool_stats["solves_per_s"] / serial_stats["solves_per_s"]},
+            "burst": {"pool": pool_stats, "one_at_a_time": serial_stats, "one_at_a_time_all_f64": serial64_stats,
+                      "speedup_solves_per_s": pool_stats["solves_per_s"] / serial_stats["solves_per_s"],
+                      "speedup_vs_f64_one_at_a_time": pool_stats["solves_per_s"] / serial64_stats["solves_per_s"]},
             "poisson_half_capacity": {"rate_per_s": rate, "pool": pool_rate_stats}}
+
+
+def energy_block(r64, r32, work, t64_ms, t32_ms):
+    out = {}
+    for name, r, t in (("f64", r64, t64_ms), ("f32", r32, t32_ms)):
+        p = (r["clocks"] or {}).get("power_w")
+        if p:
+            out[name] = {"power_w_median": p, "joules_per_dof_update": p * t * 1e-3 / work,
+                         "dof_updates_per_joule": work / (p * t * 1e-3)}
+    return out or None
 
 
 def run_ours(args, world, rank, dev, pg):
@@ -337,16 +358,20 @@ def run_ours(args, world, rank, dev, pg):
         "roofline": {"bound": "alu", "achieved": ach64, "peak": p64, "unit": "TFLOP/s", "frac": ach64 / p64,
                      "traffic": None, "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},double>",
                      "peak_note": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop at the max SM clock (derived)",
-                     "stage_ms": r64["stage_ms"], "elems_per_block": r64["epb"]},
+                     "stage_ms": r64["stage_ms"], "elems_per_block": r64["epb"],
+                     "mapping": r64["kernel"]},
         "f32": {"value": value32, "unit": "DOF-updates/s", "ms_per_step": t32 / args.steps,
                 "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
                              "frac": ach32 / hbm, "traffic": None, "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},float>",
                              "peak_kind": peak_kind, "stage_ms": r32["stage_ms"],
-                             "elems_per_block": r32["epb"],
+                             "elems_per_block": r32["epb"], "mapping": r32["kernel"],
                              "note": ("working set 4 x %.1f MB %s the 126 MB L2" % (
                                  r32["state_bytes"] / 1e6,
                                  "fits" if 4 * r32["state_bytes"] < 126e6 else "exceeds"))}},
         "clocks": r64["clocks"],
+        # energy per DOF-update from the measured board power during the timed region (the paper's
+        # energy comparison, Sec. 3.3, multiplies TDP by run time instead)
+        "energy": energy_block(r64, r32, work, t64, t32),
         "check": {"l2_norm_f64": r64["l2_norm"], "l2_norm_f32": r32["l2_norm"], "mass_f64": r64["mass"]},
     }
     if rank == 0 and not args.no_cpu_baseline:
