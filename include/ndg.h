@@ -213,6 +213,30 @@ int ndg_batch_create(ndg_ctx* const* ctxs, int n, ndg_batch** out);
 int ndg_batch_step(ndg_batch* b, const double* dts, int nsteps, int rk_scheme);
 int ndg_batch_destroy(ndg_batch* b);
 
+/* ---- domain decomposition: one solve split into rectangular partitions --------------------- */
+/* The paper distributes the element grid over rectangular/cuboid subdomains and exchanges the
+ * border values every RK sub-step (Sec. 3.2).  ndg_partition emulates that on one GPU: the global
+ * problem gcfg (stream ignored) is split into parts[0] x parts[1] x parts[2] blocks (as even as
+ * possible; parts[a] in 1..elems[a], axes >= dim ignored); each block is a solve with its own
+ * arrays and halo buffers; before every stage a pack kernel writes every block's boundary traces
+ * (n^(dim-1) face values per boundary element and variable) into its neighbours' halos -- the
+ * buffers a multi-GPU version would send and receive -- and one batched stage launch advances all
+ * blocks.  Results are bitwise those of the unpartitioned solve. */
+typedef struct ndg_partition ndg_partition;
+int ndg_partition_create(const ndg_config* gcfg, const int parts[3], ndg_partition** out);
+/* Global state in element layout of the whole problem (host or device source), scattered to the
+ * blocks on the device.  Waits for the copy. */
+int ndg_partition_set_state(ndg_partition* p, const void* src, size_t nbytes, int src_on_device);
+/* Gathers the blocks into the global element layout.  Waits for the copy. */
+int ndg_partition_get_state(ndg_partition* p, void* dst, size_t nbytes, int dst_on_device);
+/* nsteps steps of scheme rk: one graph replay per step (exchange + stage launch per stage). */
+int ndg_partition_step(ndg_partition* p, double dt, int nsteps, int rk_scheme);
+/* Norms of the whole state, combined from the blocks in a fixed order (no reference). */
+int ndg_partition_norms(ndg_partition* p, ndg_norms_t* out);
+/* Element offset and element counts of block `part` (blocks numbered x fastest). */
+int ndg_partition_info(const ndg_partition* p, int part, int offset[3], int elems[3]);
+int ndg_partition_destroy(ndg_partition* p);
+
 /* ---- serving: continuous batching of independent solves under a memory budget -------------- */
 typedef struct {
   double submit_s;    /* host time of submission (seconds, steady clock) */

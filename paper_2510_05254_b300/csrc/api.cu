@@ -513,6 +513,14 @@ int capture_step(const std::vector<Group*>& groups, int rk, cudaStream_t cap, cu
 
 bool valid_rk(int rk) { return rk == 3 || rk == 4 || rk == 6; }
 
+SolveDesc ndg_ctx_desc(const ndg_ctx* c) { return c->desc; }
+int ndg_ctx_ensure_buffers(ndg_ctx* c, int rk) { return ensure_buffers(c, rk); }
+void ndg_ctx_mark_state(ndg_ctx* c) {
+  c->have_state = true;
+  c->t = 0.0;
+  c->steps = 0;
+}
+
 int check_config(const ndg_config& k) {
   if (k.dim < 1 || k.dim > 3) return fail(NDG_EINVAL, "dim must be 1, 2 or 3 (got %d)", k.dim);
   if (k.degree < 1 || k.degree > kMaxDegree)

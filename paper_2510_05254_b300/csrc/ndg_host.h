@@ -49,6 +49,12 @@ struct TileConfig {
 TileConfig default_tile(const KernelClass& kc);
 TileConfig tuned_tile(const KernelClass& kc);  // epb == 0 when the class was never tuned
 
+// Accessors of a context for the partition emulation: its descriptor (buffers, geometry, dt),
+// its RK buffers for scheme rk, and marking its state as set by a device-side copy.
+SolveDesc ndg_ctx_desc(const ndg_ctx* c);
+int ndg_ctx_ensure_buffers(ndg_ctx* c, int rk);
+void ndg_ctx_mark_state(ndg_ctx* c);
+
 // Geometry part of a solve descriptor (scales, lift coefficients, element counts).
 void fill_solve_geometry(const ndg_config& cfg, const Basis& b, SolveDesc* d);
 // Validate a configuration (no device access); NDG_OK or NDG_EINVAL with a message.

@@ -64,6 +64,11 @@ struct SolveDesc {
   // FP32 copies of the geometric coefficients above (an FP32 kernel must not spend FP64
   // operations -- 1/64 of the FP32 rate on B300 -- converting them per node)
   float f_vol_scale[3], f_lift_lo[3], f_lift_hi[3], f_c2, f_c;
+  // Partitioned solves: traces of the neighbouring partition across the low / high boundary
+  // along each axis, layout [v][transverse element][face node] (face node = the index of the
+  // line through it); NULL = periodic wrap inside this solve.
+  const void* halo_lo[3];
+  const void* halo_hi[3];
 };
 
 // Header of a launch's work list (device memory): tiles are numbered across all solves.

@@ -84,6 +84,8 @@ struct SolveRegs {
   real vs[DIM], qlo[DIM], qhi[DIM];
   real c, c2;
   real a_self, bdt, dts;  // a_self * dt', b * dt', dt' = dt * rhs_scale
+  const real* halo_lo[DIM];
+  const real* halo_hi[DIM];
 
   __device__ __forceinline__ void load(const SolveDesc* sd, int i, const StagePlan& plan) {
     index = i;
@@ -102,6 +104,8 @@ struct SolveRegs {
       vs[a] = Coef<real>::vol(sd, a);
       qlo[a] = Coef<real>::lo(sd, a);
       qhi[a] = Coef<real>::hi(sd, a);
+      halo_lo[a] = static_cast<const real*>(sd->halo_lo[a]);
+      halo_hi[a] = static_cast<const real*>(sd->halo_hi[a]);
     }
     c = Coef<real>::c(sd);
     c2 = Coef<real>::c2(sd);
@@ -276,31 +280,42 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         } else {
           pbase = line % n + (n + 1) * (line / n); pstride = (n + 1) * n; ubase = line; ustride = n * n;
         }
-        // periodic neighbours along axis a (element indices fit in 32 bits, checked at creation)
+        // periodic neighbours along axis a (element indices fit in 32 bits, checked at creation);
+        // on a partition boundary with a halo the neighbour's trace comes from the halo instead
         long long elo, ehi;
+        bool lo_halo = false, hi_halo = false;
+        long long hoff = 0;  // offset of this line's face node in a halo of axis a (variable 0)
+        long long hvs = 0;   // halo stride between variables
         {
           const unsigned eu = (unsigned)(e0 + el);
           const unsigned U0 = S.E0, U1 = S.E1;
-          unsigned lo_, hi_;
+          unsigned lo_, hi_, te, ca, Ea;
           if (a == 0) {
             const unsigned ex = eu % U0;
+            ca = ex; Ea = U0; te = eu / U0;
             lo_ = eu - ex + (ex == 0 ? U0 - 1 : ex - 1);
             hi_ = eu - ex + (ex == U0 - 1 ? 0 : ex + 1);
           } else if (a == 1) {
             const unsigned ey = (eu / U0) % U1;
+            ca = ey; Ea = U1; te = eu % U0 + U0 * (eu / (U0 * U1));
             lo_ = ey == 0 ? eu + (U1 - 1) * U0 : eu - U0;
             hi_ = ey == U1 - 1 ? eu - (U1 - 1) * U0 : eu + U0;
           } else {
             const unsigned step = U0 * U1, U2 = S.E2;
             const unsigned ez = eu / step;
+            ca = ez; Ea = U2; te = eu % step;
             lo_ = ez == 0 ? eu + (U2 - 1) * step : eu - step;
             hi_ = ez == U2 - 1 ? eu - (U2 - 1) * step : eu + step;
           }
           elo = lo_;
           ehi = hi_;
+          lo_halo = ca == 0 && S.halo_lo[a] != nullptr;
+          hi_halo = ca == Ea - 1 && S.halo_hi[a] != nullptr;
+          hoff = (long long)te * L + line;
+          hvs = (long long)(nelem / Ea) * L;
         }
-        const bool lo_in = elo >= e0 && elo < e0 + cnt;
-        const bool hi_in = ehi >= e0 && ehi < e0 + cnt;
+        const bool lo_in = !lo_halo && elo >= e0 && elo < e0 + cnt;
+        const bool hi_in = !hi_halo && ehi >= e0 && ehi < e0 + cnt;
         const real* sUe = sU + el * SPE + pbase;
         real* sRe = sR + el * SPE + pbase;
         const real vs = S.vs[a];
@@ -313,8 +328,10 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           const bool has_lo = qlo != real(0), has_hi = qhi != real(0);
           real xlo = 0, xhi = 0;
           if (has_lo)
-            xlo = lo_in ? sU[(int)(elo - e0) * SPE + pbase + N * pstride] : uin[elo * NPE + ubase + N * ustride];
-          if (has_hi) xhi = hi_in ? sU[(int)(ehi - e0) * SPE + pbase] : uin[ehi * NPE + ubase];
+            xlo = lo_halo ? S.halo_lo[a][hoff]
+                          : (lo_in ? sU[(int)(elo - e0) * SPE + pbase + N * pstride] : uin[elo * NPE + ubase + N * ustride]);
+          if (has_hi)
+            xhi = hi_halo ? S.halo_hi[a][hoff] : (hi_in ? sU[(int)(ehi - e0) * SPE + pbase] : uin[ehi * NPE + ubase]);
           real f[n], out[n];
 #pragma unroll
           for (int l = 0; l < n; ++l) f[l] = sUe[l * pstride];
@@ -331,10 +348,11 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           real xlo[NV], xhi[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            xlo[v] = lo_in ? sU[(v * epb + (int)(elo - e0)) * SPE + pbase + N * pstride]
-                           : uin[v * vstride + elo * NPE + ubase + N * ustride];
-            xhi[v] = hi_in ? sU[(v * epb + (int)(ehi - e0)) * SPE + pbase]
-                           : uin[v * vstride + ehi * NPE + ubase];
+            xlo[v] = lo_halo ? S.halo_lo[a][v * hvs + hoff]
+                             : (lo_in ? sU[(v * epb + (int)(elo - e0)) * SPE + pbase + N * pstride]
+                                      : uin[v * vstride + elo * NPE + ubase + N * ustride]);
+            xhi[v] = hi_halo ? S.halo_hi[a][v * hvs + hoff]
+                             : (hi_in ? sU[(v * epb + (int)(ehi - e0)) * SPE + pbase] : uin[v * vstride + ehi * NPE + ubase]);
           }
           const real* sVa = sV + a * epb * SPE + el * SPE + pbase;
           const real c2 = S.c2;

@@ -84,6 +84,13 @@ _SIGS = {
     "ndg_batch_create": [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)],
     "ndg_batch_step": [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int],
     "ndg_batch_destroy": [_P],
+    "ndg_partition_create": [ctypes.POINTER(ndg_config), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P)],
+    "ndg_partition_set_state": [_P, _P, ctypes.c_size_t, ctypes.c_int],
+    "ndg_partition_get_state": [_P, _P, ctypes.c_size_t, ctypes.c_int],
+    "ndg_partition_step": [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int],
+    "ndg_partition_norms": [_P, ctypes.POINTER(ndg_norms_t)],
+    "ndg_partition_info": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "ndg_partition_destroy": [_P],
     "ndg_pool_create": [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)],
     "ndg_pool_submit": [_P, ctypes.POINTER(ndg_config), _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_double,
                         ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
@@ -252,6 +259,42 @@ def ndg_batch_step(batch, dts, nsteps: int, rk: int = NDG_RK4) -> None:
 
 def ndg_batch_destroy(batch) -> None:
     _call("ndg_batch_destroy", batch)
+
+
+def ndg_partition_create(cfg: ndg_config, parts) -> int:
+    h = _P()
+    arr = (ctypes.c_int * 3)(*(list(parts) + [1] * (3 - len(parts))))
+    _call("ndg_partition_create", ctypes.byref(cfg), arr, ctypes.byref(h))
+    return h.value
+
+
+def ndg_partition_set_state(part, ptr: int, nbytes: int, on_device: bool) -> None:
+    _call("ndg_partition_set_state", part, ptr, nbytes, int(on_device))
+
+
+def ndg_partition_get_state(part, ptr: int, nbytes: int, on_device: bool) -> None:
+    _call("ndg_partition_get_state", part, ptr, nbytes, int(on_device))
+
+
+def ndg_partition_step(part, dt: float, nsteps: int, rk: int = NDG_RK4) -> None:
+    _call("ndg_partition_step", part, float(dt), int(nsteps), int(rk))
+
+
+def ndg_partition_norms(part) -> ndg_norms_t:
+    out = ndg_norms_t()
+    _call("ndg_partition_norms", part, ctypes.byref(out))
+    return out
+
+
+def ndg_partition_info(part, index: int):
+    o = (ctypes.c_int * 3)()
+    e = (ctypes.c_int * 3)()
+    _call("ndg_partition_info", part, index, o, e)
+    return list(o), list(e)
+
+
+def ndg_partition_destroy(part) -> None:
+    _call("ndg_partition_destroy", part)
 
 
 def ndg_pool_create(budget_bytes: int, device: int = 0) -> int:
