@@ -49,7 +49,13 @@ enum {
 enum { NDG_ADVECTION = 0, NDG_ISO_EULER = 1 };   /* Eq. (advection2d), Eq. (eulerIso2d) */
 enum { NDG_FLUX_UPWIND = 0, NDG_FLUX_LLF = 1 };  /* Eq. (LF); upwind is valid for advection only */
 enum { NDG_RK3 = 3, NDG_RK4 = 4, NDG_RK6 = 6 };  /* Eq. (RK3), Eq. (RK4), Eq. (RK6) */
-enum { NDG_F64 = 0, NDG_F32 = 1 };               /* state/arithmetic precision on the GPU */
+/* Precision of the GPU path.  NDG_F64: FP64 state and arithmetic.  NDG_F32: FP32 state and
+ * arithmetic (norms accumulate in FP64).  NDG_F64_FF: FP64 state, fluxes, face terms and stage
+ * update, with the D contraction in float-float (unevaluated sums of two floats) on the FP32
+ * pipe -- on B300 an FP64 operation costs 64 FP32 ones -- accurate to ~2^-44 of sum |D||F|
+ * (within 1e-12 relative per step of the FP64 path); a line holding a value outside
+ * [2^-74, 2^127] in magnitude is contracted in FP64.  The paper computes in FP64 throughout. */
+enum { NDG_F64 = 0, NDG_F32 = 1, NDG_F64_FF = 2 };
 enum { NDG_LAYOUT_ELEMENT = 0, NDG_LAYOUT_GRID = 1 };
 /* Thread mapping of the stage kernel (identical arithmetic, bitwise-identical results):
  * LINE = one thread per line of nodes for all variables (fewest FP64 operations),
@@ -69,7 +75,7 @@ typedef struct {
   int elems[3];       /* elements per axis, >= 1 (axes >= dim ignored) */
   int equation;       /* NDG_ADVECTION or NDG_ISO_EULER */
   int flux;           /* NDG_FLUX_UPWIND (advection) or NDG_FLUX_LLF (both equations) */
-  int dtype;          /* NDG_F64 or NDG_F32 */
+  int dtype;          /* NDG_F64, NDG_F32 or NDG_F64_FF */
   double length[3];   /* periodic domain [0, length[a]] per axis; default 1 */
   double velocity[3]; /* advection velocity a (advection only); default (1, 0, 0) */
   double sound_speed; /* isothermal sound speed c (Euler only); default 1 */
@@ -95,7 +101,7 @@ typedef struct {
   int nodes_per_elem;  /* n^dim */
   int64_t nelem;       /* product of elems[a] over a < dim */
   int64_t ndof;        /* nvar * nelem * nodes_per_elem */
-  size_t state_bytes;  /* ndof * sizeof(real) */
+  size_t state_bytes;  /* ndof * 8 (FP64, FP64_FF) or ndof * 4 (FP32) */
   size_t device_bytes; /* device memory the context holds now */
   int elems_per_block; /* stage-kernel tile in use */
   int kernel;          /* stage-kernel mapping in use: NDG_KERNEL_LINE or NDG_KERNEL_LINE_VAR */

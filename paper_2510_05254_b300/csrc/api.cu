@@ -33,23 +33,29 @@ NDG_DECL(stage_f64_d3)
 NDG_DECL(stage_f32_d1)
 NDG_DECL(stage_f32_d2)
 NDG_DECL(stage_f32_d3)
+NDG_DECL(stage_f64ff_d1)
+NDG_DECL(stage_f64ff_d2)
+NDG_DECL(stage_f64ff_d3)
 #undef NDG_DECL
 
 namespace {
 LaunchFn pick_launch(const KernelClass& k) {
-  static LaunchFn (*t[2][3])(int, int) = {{stage_f64_d1_launch, stage_f64_d2_launch, stage_f64_d3_launch},
-                                          {stage_f32_d1_launch, stage_f32_d2_launch, stage_f32_d3_launch}};
+  static LaunchFn (*t[3][3])(int, int) = {{stage_f64_d1_launch, stage_f64_d2_launch, stage_f64_d3_launch},
+                                          {stage_f32_d1_launch, stage_f32_d2_launch, stage_f32_d3_launch},
+                                          {stage_f64ff_d1_launch, stage_f64ff_d2_launch, stage_f64ff_d3_launch}};
   return t[k.dtype][k.dim - 1](k.degree, k.equation);
 }
 PrepareFn pick_prepare(const KernelClass& k) {
-  static PrepareFn (*t[2][3])(int, int) = {
+  static PrepareFn (*t[3][3])(int, int) = {
       {stage_f64_d1_prepare, stage_f64_d2_prepare, stage_f64_d3_prepare},
-      {stage_f32_d1_prepare, stage_f32_d2_prepare, stage_f32_d3_prepare}};
+      {stage_f32_d1_prepare, stage_f32_d2_prepare, stage_f32_d3_prepare},
+      {stage_f64ff_d1_prepare, stage_f64ff_d2_prepare, stage_f64ff_d3_prepare}};
   return t[k.dtype][k.dim - 1](k.degree, k.equation);
 }
 ShapeFn pick_shape(const KernelClass& k) {
-  static ShapeFn (*t[2][3])(int, int) = {{stage_f64_d1_shape, stage_f64_d2_shape, stage_f64_d3_shape},
-                                         {stage_f32_d1_shape, stage_f32_d2_shape, stage_f32_d3_shape}};
+  static ShapeFn (*t[3][3])(int, int) = {{stage_f64_d1_shape, stage_f64_d2_shape, stage_f64_d3_shape},
+                                         {stage_f32_d1_shape, stage_f32_d2_shape, stage_f32_d3_shape},
+                                         {stage_f64ff_d1_shape, stage_f64ff_d2_shape, stage_f64ff_d3_shape}};
   return t[k.dtype][k.dim - 1](k.degree, k.equation);
 }
 }  // namespace
@@ -314,7 +320,7 @@ TileConfig default_tile(const KernelClass& kc) {
 std::mutex g_tune_mu;
 std::map<long long, TileConfig> g_tuned;
 long long class_key(const KernelClass& k) {
-  return ((long long)k.dim * 16 + k.degree) * 4 + k.equation * 2 + k.dtype;
+  return (((long long)k.dim * 16 + k.degree) * 2 + k.equation) * 4 + k.dtype;
 }
 // Optional persistent cache: NDG_AUTOTUNE_CACHE names a text file of lines
 // "dim degree equation dtype epb variant", read once per process, rewritten after each autotune.
@@ -340,7 +346,7 @@ void save_tune_cache_locked() {
   if (!f) return;
   for (auto& kv : g_tuned) {
     long long key = kv.first;
-    const int dtype = (int)(key % 2), eq = (int)((key / 2) % 2), deg = (int)((key / 4) % 16), dim = (int)(key / 64);
+    const int dtype = (int)(key % 4), eq = (int)((key / 4) % 2), deg = (int)((key / 8) % 16), dim = (int)(key / 128);
     std::fprintf(f, "%d %d %d %d %d %d\n", dim, deg, eq, dtype, kv.second.epb, kv.second.variant);
   }
   std::fclose(f);
@@ -531,7 +537,8 @@ int check_config(const ndg_config& k) {
     return fail(NDG_EINVAL, "unknown flux %d", k.flux);
   if (k.equation == NDG_ISO_EULER && k.flux != NDG_FLUX_LLF)
     return fail(NDG_EINVAL, "isothermal Euler takes the local Lax-Friedrichs flux");
-  if (k.dtype != NDG_F64 && k.dtype != NDG_F32) return fail(NDG_EINVAL, "unknown dtype %d", k.dtype);
+  if (k.dtype != NDG_F64 && k.dtype != NDG_F32 && k.dtype != NDG_F64_FF)
+    return fail(NDG_EINVAL, "unknown dtype %d", k.dtype);
   for (int a = 0; a < k.dim; ++a) {
     if (k.elems[a] < 1) return fail(NDG_EINVAL, "elems[%d] must be >= 1", a);
     if (!(k.length[a] > 0.0) || !std::isfinite(k.length[a]))
@@ -629,7 +636,7 @@ int ndg_create_ex(const ndg_config* cfg, ndg_ctx** out) {
   c->nvar = k.equation == NDG_ADVECTION ? 1 : k.dim + 1;
   c->nelem = nelem;
   c->ndof = nelem * c->npe * c->nvar;
-  c->esize = k.dtype == NDG_F64 ? 8 : 4;
+  c->esize = dtype_bytes(k.dtype);
   c->state_bytes = (size_t)c->ndof * c->esize;
   if (!build_basis(k.degree, &c->basis)) {
     delete c;

@@ -85,6 +85,10 @@ struct GroupHeader {
 // shared memory (higher occupancy for the multi-variable Euler classes).
 enum { kLineKernel = 0, kLineVarKernel = 1 };
 
+// Bytes per state value of a precision code (NDG_F64, NDG_F32, NDG_F64_FF): FP32 is the only
+// 4-byte one.
+inline int dtype_bytes(int dtype) { return dtype == 1 ? 4 : 8; }
+
 // Kernel class: everything that is a template parameter of the stage kernel.
 struct KernelClass {
   int dim, degree, equation, dtype;

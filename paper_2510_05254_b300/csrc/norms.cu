@@ -149,7 +149,7 @@ int launch_norms(int dtype, int dim, int degree, int equation, const void* U, co
   a.adv_speed = 0.0;
   for (int d = 0; d < dim; ++d) a.adv_speed += std::fabs(velocity[d]);
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == 0) norms_partial<double><<<nblocks, 256, 0, s>>>(a, partials);
+  if (dtype_bytes(dtype) == 8) norms_partial<double><<<nblocks, 256, 0, s>>>(a, partials);
   else norms_partial<float><<<nblocks, 256, 0, s>>>(a, partials);
   norms_final<<<1, 32, 0, s>>>(partials, nblocks, a.adv_speed, equation, result);
   return (int)cudaGetLastError();
@@ -167,7 +167,7 @@ int launch_relayout(int dtype, int dim, int degree, int nvar, const int* E, cons
   if (blocks > 148 * 16) blocks = 148 * 16;
   if (blocks < 1) blocks = 1;
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == 0)
+  if (dtype_bytes(dtype) == 8)
     relayout_kernel<double><<<(int)blocks, threads, 0, s>>>((const double*)src, (double*)dst, total,
                                                             n, npe, dim, E0, E1, E2, to_element);
   else

@@ -140,7 +140,7 @@ int launch_pack(ndg_partition* P, int role, cudaStream_t s) {
   if (P->pack_total == 0) return NDG_OK;
   long long blocks = (P->pack_total + 255) / 256;
   blocks = std::min<long long>(blocks, 148 * 8);
-  if (P->global.dtype == NDG_F64)
+  if (dtype_bytes(P->global.dtype) == 8)
     pack_traces<double><<<(int)blocks, 256, 0, s>>>(P->group.d_desc, P->d_items, (int)P->h_items.size(),
                                                      P->pack_total, role, P->global.dim, P->n, P->nvar);
   else
@@ -157,7 +157,7 @@ int copy_parts(ndg_partition* P, bool to_part) {
     void* part = P->group.h_desc[p].buf[kUN];
     const int* o = &P->off[3 * p];
     const int* c = &P->cnt[3 * p];
-    if (P->global.dtype == NDG_F64)
+    if (dtype_bytes(P->global.dtype) == 8)
       subbox_copy<double><<<blocks, 256, 0, P->stream>>>((double*)P->d_global, (double*)part, to_part, P->npe,
                                                          P->nvar, P->global.elems[0], P->global.elems[1],
                                                          P->global.elems[2], o[0], o[1], o[2], c[0], c[1], c[2]);
@@ -195,7 +195,7 @@ int ndg_partition_create(const ndg_config* gcfg, const int parts[3], ndg_partiti
   P->npe = 1;
   for (int a = 0; a < gcfg->dim; ++a) P->npe *= P->n;
   P->nvar = gcfg->equation == NDG_ADVECTION ? 1 : gcfg->dim + 1;
-  P->esize = gcfg->dtype == NDG_F64 ? 8 : 4;
+  P->esize = dtype_bytes(gcfg->dtype);
   long long gel = (long long)P->global.elems[0] * P->global.elems[1] * P->global.elems[2];
   P->global_bytes = (size_t)gel * P->npe * P->nvar * P->esize;
   cudaSetDevice(gcfg->device);

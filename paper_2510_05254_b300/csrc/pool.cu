@@ -61,7 +61,7 @@ struct PoolSolve {
 };
 
 long long pool_class_key(const KernelClass& k, int rk) {
-  return (((long long)k.dim * 16 + k.degree) * 4 + k.equation * 2 + k.dtype) * 8 + rk;
+  return ((((long long)k.dim * 16 + k.degree) * 2 + k.equation) * 4 + k.dtype) * 8 + rk;
 }
 
 struct PoolClass {
@@ -423,7 +423,7 @@ int ndg_pool_submit(ndg_pool* p, const ndg_config* cfg, const void* u0, size_t n
   long long nelem = 1;
   for (int a = 0; a < cfg->dim; ++a) nelem *= cfg->elems[a];
   if (nelem > 0x7fffffffLL) return fail(NDG_EINVAL, "more than 2^31 - 1 elements");
-  s->state_bytes = (size_t)ndof * (cfg->dtype == NDG_F64 ? 8 : 4);
+  s->state_bytes = (size_t)ndof * dtype_bytes(cfg->dtype);
   if (nbytes != s->state_bytes)
     return fail(NDG_EINVAL, "state size mismatch: got %zu bytes, expected %zu", nbytes, s->state_bytes);
   s->need = s->state_bytes * num_roles_for(rk);

@@ -10,6 +10,38 @@ namespace ndg {
 
 namespace {
 
+#ifndef NDG_FF
+#define NDG_FF false
+#endif
+
+const BasisFF& basis_ff(int N) {
+  static BasisFF table[kMaxDegree + 1];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    auto sp = [](double d, float& h, float& l) {
+      h = (float)d;
+      l = (float)(d - (double)h);
+    };
+    for (int d = 1; d <= kMaxDegree; ++d) {
+      Basis b;
+      build_basis(d, &b);
+      BasisFF& t = table[d];
+      std::memset(&t, 0, sizeof(t));
+      const int n = d + 1, h = n / 2;
+      for (int i = 0; i < h; ++i)
+        for (int m = 0; m < h; ++m) {
+          sp(b.Ae[i * kMaxN + m], t.Aeh[i * 4 + m], t.Ael[i * 4 + m]);
+          sp(b.Bo[i * kMaxN + m], t.Boh[i * 4 + m], t.Bol[i * 4 + m]);
+        }
+      for (int i = 0; i < h; ++i) {
+        sp(b.Cmid[i], t.Cmidh[i], t.Cmidl[i]);
+        sp(b.Dmid[i], t.Dmidh[i], t.Dmidl[i]);
+      }
+    }
+  });
+  return table[N];
+}
+
 template <typename real>
 const BasisArgs<real>& basis_args(int N) {
   static BasisArgs<real> table[kMaxDegree + 1];
@@ -45,7 +77,7 @@ void shape_of(int variant, int epb, int* threads, size_t* smem) {
 
 template <int N, int EQ, bool VS>
 void launch_kernel(int grid, int threads, size_t smem, void* stream, const StageArgs<NDG_REAL>& args) {
-  stage_kernel<NDG_DIM, N, EQ, NDG_REAL, VS><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
+  stage_kernel<NDG_DIM, N, EQ, NDG_REAL, VS, NDG_FF><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
 }
 
 template <int N, int EQ>
@@ -56,6 +88,7 @@ int launch_one(int variant, int grid, int epb, const SolveDesc* solves, const Gr
   args.hdr = header;
   args.plan = plan;
   args.basis = basis_args<NDG_REAL>(N);
+  args.bff = basis_ff(N);
   int threads;
   size_t smem;
   shape_of<N, EQ>(variant, epb, &threads, &smem);
@@ -67,8 +100,8 @@ int launch_one(int variant, int grid, int epb, const SolveDesc* solves, const Gr
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaFuncAttributes fa{};
-    if (variant == kLineVarKernel) cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL, true>);
-    else cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL, false>);
+    if (variant == kLineVarKernel) cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF>);
+    else cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF>);
     launch_error_detail(grid, threads, smem, fa.maxThreadsPerBlock, fa.numRegs, fa.localSizeBytes,
                         fa.maxDynamicSharedSizeBytes);
   }
@@ -96,8 +129,8 @@ int prepare_one(int variant, int epb, int* max_blocks) {
   shape_of<N, EQ>(variant, epb, &threads, &smem);
   if (threads > 1024 || threads < 1) return (int)cudaErrorInvalidConfiguration;
   if (variant == kLineVarKernel)
-    return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL, true>, threads, smem, max_blocks);
-  return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL, false>, threads, smem, max_blocks);
+    return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF>, threads, smem, max_blocks);
+  return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF>, threads, smem, max_blocks);
 }
 
 template <int N, int EQ>

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "ndg_internal.h"
+#include "stage_ff.cuh"
 
 namespace ndg {
 
@@ -48,6 +49,7 @@ struct StageArgs {
   const GroupHeader* hdr;
   StagePlan plan;
   BasisArgs<real> basis;
+  BasisFF bff;  // float-float halves of the same tables (FP64 path with float-float contraction)
 };
 
 // Per-solve coefficients in the kernel's precision (no conversion in device code).
@@ -177,6 +179,26 @@ __device__ __forceinline__ void contract_even_odd(const real (&f)[N + 1], real (
   }
 }
 
+// D along one line: FP64 / FP32 even-odd products, or (FF) the float-float version of the same,
+// with the FP64 one for a line holding a value that cannot be split into normal floats.
+template <int N, typename real, bool FF>
+__device__ __forceinline__ void contract_line(const real (&f)[N + 1], real (&out)[N + 1], const StageArgs<real>& args) {
+  if constexpr (FF) {
+    ff fd[N + 1];
+    bool ok = true;
+#pragma unroll
+    for (int l = 0; l <= N; ++l) ok = ff_split(f[l], fd[l].h, fd[l].l) && ok;
+    if (ok) {
+      ff od[N + 1];
+      contract_even_odd_ff<N>(fd, od, args.bff);
+#pragma unroll
+      for (int l = 0; l <= N; ++l) out[l] = ff_to_double(od[l]);
+      return;
+    }
+  }
+  contract_even_odd<N>(f, out, args.basis);
+}
+
 template <int DIM, int N, int EQ, typename real, bool VS = false>
 struct StageGeom {
   static constexpr int n = N + 1;
@@ -195,7 +217,7 @@ struct StageGeom {
 // of the face flux are computed once per line).  VS = true: a thread owns one (line, variable)
 // pair, so an Euler CTA has nvar times more threads for the same shared memory; the operations
 // per variable are the same, in the same order, so the results are bitwise identical.
-template <int DIM, int N, int EQ, typename real, bool VS>
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
 __global__ void stage_kernel(const StageArgs<real> args) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
@@ -335,7 +357,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           real f[n], out[n];
 #pragma unroll
           for (int l = 0; l < n; ++l) f[l] = sUe[l * pstride];
-          contract_even_odd<N>(f, out, args.basis);
+          contract_line<N, real, FF>(f, out, args);
 #pragma unroll
           for (int l = 0; l < n; ++l) {
             real r = (a == 0) ? (unit ? out[l] : vs * out[l]) : fma(vs, out[l], sRe[l * pstride]);
@@ -382,7 +404,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
 #pragma unroll
               for (int l = 0; l < n; ++l) f[l] = sUv[l * pstride] * sVa[l * pstride];
             }
-            contract_even_odd<N>(f, out, args.basis);
+            contract_line<N, real, FF>(f, out, args);
             real fxlo, fxhi;
             if (v == 0) {
               fxlo = xlo[1 + a];

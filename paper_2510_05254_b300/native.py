@@ -18,7 +18,7 @@ NDG_OK, NDG_EINVAL, NDG_ENOMEM, NDG_ECUDA, NDG_ENONFINITE, NDG_EAGAIN, NDG_ETIME
 NDG_ADVECTION, NDG_ISO_EULER = 0, 1
 NDG_FLUX_UPWIND, NDG_FLUX_LLF = 0, 1
 NDG_RK3, NDG_RK4, NDG_RK6 = 3, 4, 6
-NDG_F64, NDG_F32 = 0, 1
+NDG_F64, NDG_F32, NDG_F64_FF = 0, 1, 2
 NDG_LAYOUT_ELEMENT, NDG_LAYOUT_GRID = 0, 1
 NDG_KERNEL_AUTO, NDG_KERNEL_LINE, NDG_KERNEL_LINE_VAR = 0, 1, 2
 STATUS_NAMES = {0: "NDG_OK", 1: "NDG_EINVAL", 2: "NDG_ENOMEM", 3: "NDG_ECUDA", 4: "NDG_ENONFINITE",

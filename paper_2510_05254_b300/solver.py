@@ -12,7 +12,8 @@ import torch
 
 from . import native as nat
 
-DTYPES = {"f64": (nat.NDG_F64, torch.float64, np.float64), "f32": (nat.NDG_F32, torch.float32, np.float32)}
+DTYPES = {"f64": (nat.NDG_F64, torch.float64, np.float64), "f32": (nat.NDG_F32, torch.float32, np.float32),
+          "f64ff": (nat.NDG_F64_FF, torch.float64, np.float64)}
 
 
 class Solver:

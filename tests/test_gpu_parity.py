@@ -405,3 +405,47 @@ def test_both_kernel_mappings(kernel, dim, N, E, eq):
         assert np.array_equal(outs[0], outs[1])
     ref = orc.step(p, U.astype(np.float32).astype(np.float64), dt, 2, 4)
     assert rel_l2(outs[1], ref) < 2 * F32_TOL
+
+
+# ---- FP64 state with the float-float contraction (NDG_F64_FF): the FP64 parity bar ----
+
+@pytest.mark.parametrize("N,eq", CASES_2D)
+def test_float_float_contraction_2d(N, eq):
+    p, s = make(2, N, (5, 3), eq, dtype="f64ff", epb=4, length=(1.0, 0.7, 1.0), velocity=(0.9, -0.6, 0))
+    U = initial(p)
+    dt = orc.stable_dt(p, U, 0.2)
+    check(p, s, U, dt, 2, 4, F64_TOL)
+
+
+@pytest.mark.parametrize("dim,N,E,eq,rk", [(1, 3, (9,), 0, 4), (1, 6, (7,), 1, 6), (3, 2, (3, 2, 3), 1, 4),
+                                           (3, 5, (2, 3, 2), 0, 3), (3, 3, (2, 2, 3), 1, 6), (2, 7, (4, 3), 1, 6)])
+def test_float_float_contraction_1d_3d_rk(dim, N, E, eq, rk):
+    p, s = make(dim, N, E, eq, dtype="f64ff", epb=3, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3))
+    U = initial(p)
+    dt = orc.stable_dt(p, U, 0.2)
+    check(p, s, U, dt, 3, rk, F64_TOL)
+
+
+def test_float_float_falls_back_to_fp64_for_unsplittable_values():
+    """Advection is linear: a state of magnitude 1e-25 (below 2^-74, not splittable into normal
+    floats) takes the FP64 contraction and still meets the FP64 bar; a state mixing tiny and
+    ordinary values takes either path line by line."""
+    p, s = make(2, 5, (6, 5), 0, dtype="f64ff", epb=4)
+    U = initial(p)
+    dt = orc.stable_dt(p, U, 0.2)
+    check(p, s, U * 1e-25, dt, 2, 4, F64_TOL)
+    mixed = U.copy()
+    mixed[:, ::2] *= 1e-25
+    check(p, s, mixed, dt, 2, 4, F64_TOL)
+
+
+def test_float_float_full_size_config2():
+    p = orc.Problem(dim=2, degree=7, elems=(256, 256, 1), equation=0, flux=0, velocity=(1.0, 0.5, 0))
+    X = orc.node_coords(p)
+    U0 = inputs.gaussian_noise(X)
+    dt = orc.stable_dt(p, U0, 0.1)
+    ref = orc.step(p, U0, dt, 1, 4)
+    s = Solver(2, 7, (256, 256), velocity=(1.0, 0.5, 0), dtype="f64ff")
+    s.set_state(U0)
+    s.step(dt, 1, 4)
+    assert rel_l2(s.get_state(), ref) < F64_TOL
