@@ -206,8 +206,12 @@ struct StageGeom {
   static constexpr int NPE = ipow_c(n, DIM);        // nodes per element
   static constexpr int NV = EQ == 0 ? 1 : DIM + 1;  // variables
   static constexpr int SPE = (n + 1) * L;           // padded shared slots per element
-  static constexpr int NS = EQ == 0 ? 2 * NV : 2 * NV + DIM;  // shared arrays of SPE per element
-  static constexpr int NB = 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
+  // FP64 (arithmetic-bound) stages U^n and ACC in shared memory and keeps the Euler velocities
+  // there; FP32 (memory-bound) keeps shared memory small for occupancy: U^n / ACC are
+  // prefetched into L2 and read directly, velocities are recomputed per line.
+  static constexpr bool SLIM = sizeof(real) == 4;
+  static constexpr int NS = (EQ == 0 || SLIM) ? 2 * NV : 2 * NV + DIM;  // shared arrays of SPE per element
+  static constexpr int NB = SLIM ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
   static constexpr int TPE = VS ? L * NV : L;
   __device__ static __forceinline__ int pad(int node) { return node + node / n; }
@@ -258,6 +262,15 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           const int el = idx / NPE, node = idx - el * NPE;
           cp_async_elem(dst + el * SPE + G::pad(node), src + idx);
         }
+        if constexpr (G::SLIM) {
+          // start the update's reads now: one L2 prefetch per 128-byte line of U^n / ACC
+          constexpr int per_line = 128 / (int)sizeof(real);
+          for (int idx = tid * per_line; idx < total; idx += nthr * per_line) {
+            if (need_un) asm volatile("prefetch.global.L2 [%0];" ::"l"(S.un + v * vstride + e0 * NPE + idx));
+            if (need_acc) asm volatile("prefetch.global.L2 [%0];" ::"l"(S.acc + v * vstride + e0 * NPE + idx));
+          }
+          continue;
+        }
         if (need_un) {
           const real* s2 = S.un + v * vstride + e0 * NPE;
           real* d2 = sB + v * epb * NPE;
@@ -272,8 +285,8 @@ __global__ void stage_kernel(const StageArgs<real> args) {
     }
     cp_async_wait_all();
     __syncthreads();
-    // ---- 2. velocities (Euler) ----
-    if constexpr (EQ == 1) {
+    // ---- 2. velocities (Euler; the FP32 kernel recomputes them per line instead) ----
+    if constexpr (EQ == 1 && !G::SLIM) {
       const int total = cnt * NPE;
       for (int idx = tid; idx < total; idx += nthr) {
         const int el = idx / NPE, node = idx - el * NPE;
@@ -343,9 +356,15 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         const real vs = S.vs[a];
         const real qlo = S.qlo[a];
         const real qhi = S.qhi[a];
-        // vs is exactly 1 on axis 0 unless the advection velocity has no x component
-        const bool unit = (a == 0) && vs == real(1);
+        // The right-hand side is kept divided by axis 0's scale (rhs_scale), so axis 0 needs no
+        // multiply; a zero scale means advection with no velocity along this axis: no flux.
         if constexpr (EQ == 0) {
+         if (vs == real(0)) {
+          if (a == 0) {
+#pragma unroll
+            for (int l = 0; l < n; ++l) sRe[l * pstride] = real(0);
+          }
+         } else {
           // upwinding makes one of the two face terms vanish: its trace is not even loaded
           const bool has_lo = qlo != real(0), has_hi = qhi != real(0);
           real xlo = 0, xhi = 0;
@@ -360,11 +379,12 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           contract_line<N, real, FF>(f, out, args);
 #pragma unroll
           for (int l = 0; l < n; ++l) {
-            real r = (a == 0) ? (unit ? out[l] : vs * out[l]) : fma(vs, out[l], sRe[l * pstride]);
+            real r = (a == 0) ? out[l] : fma(vs, out[l], sRe[l * pstride]);
             if (l == 0 && has_lo) r = fma(qlo, xlo - f[0], r);
             if (l == N && has_hi) r = fma(qhi, f[N] - xhi, r);
             sRe[l * pstride] = r;
           }
+         }
         } else {
           // exterior traces: node N of the low neighbour, node 0 of the high neighbour
           real xlo[NV], xhi[NV];
@@ -376,11 +396,21 @@ __global__ void stage_kernel(const StageArgs<real> args) {
             xhi[v] = hi_halo ? S.halo_hi[a][v * hvs + hoff]
                              : (hi_in ? sU[(v * epb + (int)(ehi - e0)) * SPE + pbase] : uin[v * vstride + ehi * NPE + ubase]);
           }
-          const real* sVa = sV + a * epb * SPE + el * SPE + pbase;
           const real c2 = S.c2;
           const real cs = S.c;
+          // velocity u_a along the line: from shared memory (FP64) or recomputed (FP32)
+          real ua[n];
+          if constexpr (G::SLIM) {
+            const real* sma = sUe + (1 + a) * epb * SPE;
+#pragma unroll
+            for (int l = 0; l < n; ++l) ua[l] = sma[l * pstride] / sUe[l * pstride];
+          } else {
+            const real* sVa = sV + a * epb * SPE + el * SPE + pbase;
+#pragma unroll
+            for (int l = 0; l < n; ++l) ua[l] = sVa[l * pstride];
+          }
           // normal velocities and LLF alpha at both faces of the line
-          const real un0 = sVa[0], unN = sVa[N * pstride];
+          const real un0 = ua[0], unN = ua[N];
           const real unlo = xlo[1 + a] / xlo[0];
           const real unhi = xhi[1 + a] / xhi[0];
           const real alo = fmax(fabs(unlo), fabs(un0)) + cs;
@@ -398,11 +428,10 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               for (int l = 0; l < n; ++l) f[l] = sm[l * pstride];
             } else if (v == 1 + a) {
 #pragma unroll
-              for (int l = 0; l < n; ++l)
-                f[l] = fma(sUv[l * pstride], sVa[l * pstride], c2 * sUe[l * pstride]);
+              for (int l = 0; l < n; ++l) f[l] = fma(sUv[l * pstride], ua[l], c2 * sUe[l * pstride]);
             } else {
 #pragma unroll
-              for (int l = 0; l < n; ++l) f[l] = sUv[l * pstride] * sVa[l * pstride];
+              for (int l = 0; l < n; ++l) f[l] = sUv[l * pstride] * ua[l];
             }
             contract_line<N, real, FF>(f, out, args);
             real fxlo, fxhi;
@@ -420,7 +449,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
             real* sRv = sRe + v * epb * SPE;
 #pragma unroll
             for (int l = 0; l < n; ++l) {
-              real r = (a == 0) ? (unit ? out[l] : vs * out[l]) : fma(vs, out[l], sRv[l * pstride]);
+              real r = (a == 0) ? out[l] : fma(vs, out[l], sRv[l * pstride]);
               // (Fhat_lo - F(U_0)) = 1/2 (F(ext) - F(U_0) - alpha (U_0 - ext)); qlo carries the 1/2
               if (l == 0) r = fma(qlo, fma(-alo, u0 - xlo[v], fxlo - f[0]), r);
               // (F(U_N) - Fhat_hi) = 1/2 (F(U_N) - F(ext) + alpha (ext - U_N))
@@ -453,10 +482,10 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           const long long g = goff + idx;
           const real r = sRv[s];
           if (plan.acc_mode == 3) {
-            uout[g] = fma(bdt, r, sAv[idx]);
+            uout[g] = fma(bdt, r, G::SLIM ? acc[g] : sAv[idx]);
             continue;
           }
-          const real base = plan.in == kUN ? sUv[s] : sBv[idx];
+          const real base = plan.in == kUN ? sUv[s] : (G::SLIM ? S.un[g] : sBv[idx]);
           real o = fma(a_self, r, base);
           for (int j = 0; j < plan.nread; ++j) {
             const real* kj = static_cast<const real*>(args.solves[si].buf[plan.kread[j]]);
@@ -464,7 +493,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           }
           uout[g] = o;
           if (plan.acc_mode == 1) acc[g] = fma(bdt, r, base);
-          else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, sAv[idx]);
+          else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, G::SLIM ? acc[g] : sAv[idx]);
           if (kw) kw[g] = r;  // the slope L(U_in) / rhs_scale; the combination applies a*dt*rhs_scale
         }
       }

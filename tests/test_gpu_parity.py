@@ -449,3 +449,19 @@ def test_float_float_full_size_config2():
     s.set_state(U0)
     s.step(dt, 1, 4)
     assert rel_l2(s.get_state(), ref) < F64_TOL
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f64ff"])
+@pytest.mark.parametrize("dim,N,E,vel", [(2, 5, (4, 5), (0.0, 0.7, 0.0)), (3, 3, (3, 2, 3), (0.5, 0.0, -0.3)),
+                                         (3, 2, (2, 3, 2), (0.0, 0.0, 0.9))])
+def test_advection_with_zero_velocity_components(dim, N, E, vel, dtype):
+    """An axis without velocity carries no flux: the kernel skips it (axis 0 included)."""
+    p, s = make(dim, N, E, 0, dtype=dtype, epb=3, velocity=vel)
+    U = initial(p)
+    dt = orc.stable_dt(p, U, 0.2)
+    if dtype == "f32":
+        s.set_state(U)
+        s.step(dt, 1, 4)
+        assert rel_l2(s.get_state(), orc.step(p, U.astype(np.float32).astype(np.float64), dt, 1, 4)) < F32_TOL
+    else:
+        check(p, s, U, dt, 2, 4, F64_TOL)
