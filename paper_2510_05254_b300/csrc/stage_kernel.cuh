@@ -179,6 +179,58 @@ __device__ __forceinline__ void contract_even_odd(const real (&f)[N + 1], real (
   }
 }
 
+// Where a line's two neighbour traces come from (element indices fit in 32 bits, checked at
+// creation): the periodic neighbours along axis a, or a partition halo on a partition boundary.
+struct LineTrace {
+  long long elo, ehi;   // neighbour elements
+  bool lo_halo, hi_halo;
+  long long hoff, hvs;  // halo offset of this line's face node (variable 0), stride per variable
+};
+
+template <int L>
+__device__ __forceinline__ LineTrace line_trace(int a, unsigned eu, int line, unsigned E0, unsigned E1,
+                                                unsigned E2, long long nelem, bool halo_lo, bool halo_hi) {
+  LineTrace t;
+  unsigned lo_, hi_, te, ca, Ea;
+  if (a == 0) {
+    const unsigned ex = eu % E0;
+    ca = ex; Ea = E0; te = eu / E0;
+    lo_ = eu - ex + (ex == 0 ? E0 - 1 : ex - 1);
+    hi_ = eu - ex + (ex == E0 - 1 ? 0 : ex + 1);
+  } else if (a == 1) {
+    const unsigned ey = (eu / E0) % E1;
+    ca = ey; Ea = E1; te = eu % E0 + E0 * (eu / (E0 * E1));
+    lo_ = ey == 0 ? eu + (E1 - 1) * E0 : eu - E0;
+    hi_ = ey == E1 - 1 ? eu - (E1 - 1) * E0 : eu + E0;
+  } else {
+    const unsigned step = E0 * E1;
+    const unsigned ez = eu / step;
+    ca = ez; Ea = E2; te = eu % step;
+    lo_ = ez == 0 ? eu + (E2 - 1) * step : eu - step;
+    hi_ = ez == E2 - 1 ? eu - (E2 - 1) * step : eu + step;
+  }
+  t.elo = lo_;
+  t.ehi = hi_;
+  t.lo_halo = ca == 0 && halo_lo;
+  t.hi_halo = ca == Ea - 1 && halo_hi;
+  t.hoff = (long long)te * L + line;
+  t.hvs = (long long)(nelem / Ea) * L;
+  return t;
+}
+
+// Padded shared-memory base / stride and unpadded node base / stride of line `line` along axis a.
+template <int n>
+__device__ __forceinline__ void line_geometry(int a, int line, int& pbase, int& pstride, int& ubase, int& ustride) {
+  if (a == 0) {
+    pbase = (n + 1) * line; pstride = 1; ubase = n * line; ustride = 1;
+  } else if (a == 1) {
+    const int i = line % n, k = line / n;
+    pbase = i + (n + 1) * n * k; pstride = n + 1; ubase = i + n * n * k; ustride = n;
+  } else {
+    pbase = line % n + (n + 1) * (line / n); pstride = (n + 1) * n; ubase = line; ustride = n * n;
+  }
+}
+
 // D along one line: FP64 / FP32 even-odd products, or (FF) the float-float version of the same,
 // with the FP64 one for a line holding a value that cannot be split into normal floats.
 template <int N, typename real, bool FF>
@@ -210,6 +262,9 @@ struct StageGeom {
   // there; FP32 (memory-bound) keeps shared memory small for occupancy: U^n / ACC are
   // prefetched into L2 and read directly, velocities are recomputed per line.
   static constexpr bool SLIM = sizeof(real) == 4;
+  // EARLY: neighbour-trace loads issued with the tile copy and a batched stage update (more loads
+  // in flight); it costs registers, and pays only for 1D/2D (measured: 3D and float-float lose
+  // occupancy), so 3D keeps the per-axis trace loads and the one-node-at-a-time update.
   static constexpr int NS = (EQ == 0 || SLIM) ? 2 * NV : 2 * NV + DIM;  // shared arrays of SPE per element
   static constexpr int NB = SLIM ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
@@ -225,6 +280,7 @@ template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
 __global__ void stage_kernel(const StageArgs<real> args) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
+  constexpr bool EARLY = DIM <= 2 && !FF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const GroupHeader hdr = *args.hdr;
   const int epb = hdr.epb;
@@ -283,6 +339,50 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         }
       }
     }
+    // ---- 1b. neighbour traces outside the tile: their global / halo loads are issued now, so
+    //         they are in flight together with the tile's copies ----
+    const int el_t = tid / TPE;
+    const int line_t = (tid - el_t * TPE) % L;
+    real xr_lo[DIM][NV], xr_hi[DIM][NV];  // loaded traces (variables of this line's faces)
+    int xs_lo[DIM], xs_hi[DIM];           // shared-memory offset of an in-tile trace, else -1
+    if constexpr (EARLY) {
+     if (el_t < cnt) {
+      const unsigned eu = (unsigned)(e0 + el_t);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        xs_lo[a] = xs_hi[a] = -1;
+        int pbase, pstride, ubase, ustride;
+        line_geometry<n>(a, line_t, pbase, pstride, ubase, ustride);
+        const LineTrace t = line_trace<L>(a, eu, line_t, S.E0, S.E1, S.E2, nelem, S.halo_lo[a] != nullptr,
+                                          S.halo_hi[a] != nullptr);
+        // advection: no flux along a zero-velocity axis, and upwinding zeroes one face
+        const bool need_lo = EQ == 1 || (S.vs[a] != real(0) && S.qlo[a] != real(0));
+        const bool need_hi = EQ == 1 || (S.vs[a] != real(0) && S.qhi[a] != real(0));
+        if (need_lo) {
+          if (t.lo_halo) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) xr_lo[a][v] = S.halo_lo[a][v * t.hvs + t.hoff];
+          } else if (t.elo >= e0 && t.elo < e0 + cnt) {
+            xs_lo[a] = (int)(t.elo - e0) * SPE + pbase + N * pstride;
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) xr_lo[a][v] = uin[v * vstride + t.elo * NPE + ubase + N * ustride];
+          }
+        }
+        if (need_hi) {
+          if (t.hi_halo) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) xr_hi[a][v] = S.halo_hi[a][v * t.hvs + t.hoff];
+          } else if (t.ehi >= e0 && t.ehi < e0 + cnt) {
+            xs_hi[a] = (int)(t.ehi - e0) * SPE + pbase;
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) xr_hi[a][v] = uin[v * vstride + t.ehi * NPE + ubase];
+          }
+        }
+      }
+     }
+    }
     cp_async_wait_all();
     __syncthreads();
     // ---- 2. velocities (Euler; the FP32 kernel recomputes them per line instead) ----
@@ -305,52 +405,8 @@ __global__ void stage_kernel(const StageArgs<real> args) {
       const int line = rem % L;
       const int vsel = rem / L;  // the variable this thread owns (VS), else 0
       if (el < cnt) {
-        // padded base / stride in shared memory; unpadded base / stride in global memory
         int pbase, pstride, ubase, ustride;
-        if (a == 0) {
-          pbase = (n + 1) * line; pstride = 1; ubase = n * line; ustride = 1;
-        } else if (a == 1) {
-          const int i = line % n, k = line / n;
-          pbase = i + (n + 1) * n * k; pstride = n + 1; ubase = i + n * n * k; ustride = n;
-        } else {
-          pbase = line % n + (n + 1) * (line / n); pstride = (n + 1) * n; ubase = line; ustride = n * n;
-        }
-        // periodic neighbours along axis a (element indices fit in 32 bits, checked at creation);
-        // on a partition boundary with a halo the neighbour's trace comes from the halo instead
-        long long elo, ehi;
-        bool lo_halo = false, hi_halo = false;
-        long long hoff = 0;  // offset of this line's face node in a halo of axis a (variable 0)
-        long long hvs = 0;   // halo stride between variables
-        {
-          const unsigned eu = (unsigned)(e0 + el);
-          const unsigned U0 = S.E0, U1 = S.E1;
-          unsigned lo_, hi_, te, ca, Ea;
-          if (a == 0) {
-            const unsigned ex = eu % U0;
-            ca = ex; Ea = U0; te = eu / U0;
-            lo_ = eu - ex + (ex == 0 ? U0 - 1 : ex - 1);
-            hi_ = eu - ex + (ex == U0 - 1 ? 0 : ex + 1);
-          } else if (a == 1) {
-            const unsigned ey = (eu / U0) % U1;
-            ca = ey; Ea = U1; te = eu % U0 + U0 * (eu / (U0 * U1));
-            lo_ = ey == 0 ? eu + (U1 - 1) * U0 : eu - U0;
-            hi_ = ey == U1 - 1 ? eu - (U1 - 1) * U0 : eu + U0;
-          } else {
-            const unsigned step = U0 * U1, U2 = S.E2;
-            const unsigned ez = eu / step;
-            ca = ez; Ea = U2; te = eu % step;
-            lo_ = ez == 0 ? eu + (U2 - 1) * step : eu - step;
-            hi_ = ez == U2 - 1 ? eu - (U2 - 1) * step : eu + step;
-          }
-          elo = lo_;
-          ehi = hi_;
-          lo_halo = ca == 0 && S.halo_lo[a] != nullptr;
-          hi_halo = ca == Ea - 1 && S.halo_hi[a] != nullptr;
-          hoff = (long long)te * L + line;
-          hvs = (long long)(nelem / Ea) * L;
-        }
-        const bool lo_in = !lo_halo && elo >= e0 && elo < e0 + cnt;
-        const bool hi_in = !hi_halo && ehi >= e0 && ehi < e0 + cnt;
+        line_geometry<n>(a, line, pbase, pstride, ubase, ustride);
         const real* sUe = sU + el * SPE + pbase;
         real* sRe = sR + el * SPE + pbase;
         const real vs = S.vs[a];
@@ -365,14 +421,24 @@ __global__ void stage_kernel(const StageArgs<real> args) {
             for (int l = 0; l < n; ++l) sRe[l * pstride] = real(0);
           }
          } else {
-          // upwinding makes one of the two face terms vanish: its trace is not even loaded
+          // upwinding makes one of the two face terms vanish: its trace was not even loaded
           const bool has_lo = qlo != real(0), has_hi = qhi != real(0);
           real xlo = 0, xhi = 0;
-          if (has_lo)
-            xlo = lo_halo ? S.halo_lo[a][hoff]
-                          : (lo_in ? sU[(int)(elo - e0) * SPE + pbase + N * pstride] : uin[elo * NPE + ubase + N * ustride]);
-          if (has_hi)
-            xhi = hi_halo ? S.halo_hi[a][hoff] : (hi_in ? sU[(int)(ehi - e0) * SPE + pbase] : uin[ehi * NPE + ubase]);
+          if constexpr (EARLY) {
+            if (has_lo) xlo = xs_lo[a] >= 0 ? sU[xs_lo[a]] : xr_lo[a][0];
+            if (has_hi) xhi = xs_hi[a] >= 0 ? sU[xs_hi[a]] : xr_hi[a][0];
+          } else {
+            const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), line, S.E0, S.E1, S.E2, nelem,
+                                              S.halo_lo[a] != nullptr, S.halo_hi[a] != nullptr);
+            if (has_lo)
+              xlo = t.lo_halo ? S.halo_lo[a][t.hoff]
+                              : (t.elo >= e0 && t.elo < e0 + cnt ? sU[(int)(t.elo - e0) * SPE + pbase + N * pstride]
+                                                                 : uin[t.elo * NPE + ubase + N * ustride]);
+            if (has_hi)
+              xhi = t.hi_halo ? S.halo_hi[a][t.hoff]
+                              : (t.ehi >= e0 && t.ehi < e0 + cnt ? sU[(int)(t.ehi - e0) * SPE + pbase]
+                                                                 : uin[t.ehi * NPE + ubase]);
+          }
           real f[n], out[n];
 #pragma unroll
           for (int l = 0; l < n; ++l) f[l] = sUe[l * pstride];
@@ -388,13 +454,26 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         } else {
           // exterior traces: node N of the low neighbour, node 0 of the high neighbour
           real xlo[NV], xhi[NV];
+          if constexpr (EARLY) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            xlo[v] = lo_halo ? S.halo_lo[a][v * hvs + hoff]
-                             : (lo_in ? sU[(v * epb + (int)(elo - e0)) * SPE + pbase + N * pstride]
-                                      : uin[v * vstride + elo * NPE + ubase + N * ustride]);
-            xhi[v] = hi_halo ? S.halo_hi[a][v * hvs + hoff]
-                             : (hi_in ? sU[(v * epb + (int)(ehi - e0)) * SPE + pbase] : uin[v * vstride + ehi * NPE + ubase]);
+            for (int v = 0; v < NV; ++v) {
+              xlo[v] = xs_lo[a] >= 0 ? sU[v * epb * SPE + xs_lo[a]] : xr_lo[a][v];
+              xhi[v] = xs_hi[a] >= 0 ? sU[v * epb * SPE + xs_hi[a]] : xr_hi[a][v];
+            }
+          } else {
+            const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), line, S.E0, S.E1, S.E2, nelem,
+                                              S.halo_lo[a] != nullptr, S.halo_hi[a] != nullptr);
+            const bool lo_in = !t.lo_halo && t.elo >= e0 && t.elo < e0 + cnt;
+            const bool hi_in = !t.hi_halo && t.ehi >= e0 && t.ehi < e0 + cnt;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              xlo[v] = t.lo_halo ? S.halo_lo[a][v * t.hvs + t.hoff]
+                                 : (lo_in ? sU[(v * epb + (int)(t.elo - e0)) * SPE + pbase + N * pstride]
+                                          : uin[v * vstride + t.elo * NPE + ubase + N * ustride]);
+              xhi[v] = t.hi_halo ? S.halo_hi[a][v * t.hvs + t.hoff]
+                                 : (hi_in ? sU[(v * epb + (int)(t.ehi - e0)) * SPE + pbase]
+                                          : uin[v * vstride + t.ehi * NPE + ubase]);
+            }
           }
           const real c2 = S.c2;
           const real cs = S.c;
@@ -469,6 +548,9 @@ __global__ void stage_kernel(const StageArgs<real> args) {
       real* __restrict__ acc = S.acc;
       real* __restrict__ kw = S.kw;
       const int total = cnt * NPE;
+      // each thread owns up to B nodes per variable: all of their operands are loaded first, so
+      // the loads are in flight together, then the results are computed and stored
+      constexpr int B = EARLY ? 8 : 1;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const real* sRv = sR + v * epb * SPE;
@@ -476,25 +558,39 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         const real* sBv = sB + v * epb * NPE;
         const real* sAv = sA + v * epb * NPE;
         const long long goff = v * vstride + e0 * NPE;
-        for (int idx = tid; idx < total; idx += nthr) {
-          const int el = idx / NPE, node = idx - el * NPE;
-          const int s = el * SPE + G::pad(node);
-          const long long g = goff + idx;
-          const real r = sRv[s];
-          if (plan.acc_mode == 3) {
-            uout[g] = fma(bdt, r, G::SLIM ? acc[g] : sAv[idx]);
-            continue;
+        for (int i0 = tid; i0 < total; i0 += nthr * B) {
+          real rr[B], bb[B], aa[B];
+#pragma unroll
+          for (int k = 0; k < B; ++k) {
+            const int idx = i0 + k * nthr;
+            if (idx >= total) break;
+            const int el = idx / NPE, node = idx - el * NPE;
+            const int s = el * SPE + G::pad(node);
+            const long long g = goff + idx;
+            rr[k] = sRv[s];
+            if (plan.acc_mode >= 2) aa[k] = G::SLIM ? acc[g] : sAv[idx];
+            if (plan.acc_mode != 3) bb[k] = plan.in == kUN ? sUv[s] : (G::SLIM ? S.un[g] : sBv[idx]);
           }
-          const real base = plan.in == kUN ? sUv[s] : (G::SLIM ? S.un[g] : sBv[idx]);
-          real o = fma(a_self, r, base);
-          for (int j = 0; j < plan.nread; ++j) {
-            const real* kj = static_cast<const real*>(args.solves[si].buf[plan.kread[j]]);
-            o = fma(S.a_read(plan, j), kj[g], o);
+#pragma unroll
+          for (int k = 0; k < B; ++k) {
+            const int idx = i0 + k * nthr;
+            if (idx >= total) break;
+            const long long g = goff + idx;
+            const real r = rr[k];
+            if (plan.acc_mode == 3) {
+              uout[g] = fma(bdt, r, aa[k]);
+              continue;
+            }
+            real o = fma(a_self, r, bb[k]);
+            for (int j = 0; j < plan.nread; ++j) {
+              const real* kj = static_cast<const real*>(args.solves[si].buf[plan.kread[j]]);
+              o = fma(S.a_read(plan, j), kj[g], o);
+            }
+            uout[g] = o;
+            if (plan.acc_mode == 1) acc[g] = fma(bdt, r, bb[k]);
+            else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, aa[k]);
+            if (kw) kw[g] = r;
           }
-          uout[g] = o;
-          if (plan.acc_mode == 1) acc[g] = fma(bdt, r, base);
-          else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, G::SLIM ? acc[g] : sAv[idx]);
-          if (kw) kw[g] = r;  // the slope L(U_in) / rhs_scale; the combination applies a*dt*rhs_scale
         }
       }
     }
