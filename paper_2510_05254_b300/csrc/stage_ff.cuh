@@ -86,7 +86,8 @@ __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.h, -b.
 // Accumulate c * x into (acc_h + acc_l): exact product of the high parts, cross terms and the
 // product's rounding error into the low accumulator.
 __device__ __forceinline__ void ff_fma_acc(float ch, float cl, ff x, float& acc_h, float& acc_l) {
-  const float p = ch * x.h;
+  const float p = __fmul_rn(ch, x.h);  // rounded on its own: contracted into the sum below, the
+                                       // product error pe would no longer be the sum's error
   const float pe = fmaf(ch, x.h, -p);
   float s, e;
   two_sum(acc_h, p, s, e);
@@ -103,7 +104,7 @@ __device__ __forceinline__ ff ff_norm(float h, float l) {
 
 // (scale as double, applied to a float-float value): used for the per-axis volume scale.
 __device__ __forceinline__ ff ff_mul(ff a, float ch, float cl) {
-  const float p = ch * a.h;
+  const float p = __fmul_rn(ch, a.h);
   const float pe = fmaf(ch, a.h, -p);
   const float l = fmaf(ch, a.l, fmaf(cl, a.h, pe));
   return ff_norm(p, l);

@@ -20,7 +20,8 @@
 //      lifted face terms at the two ends (neighbour traces from shared memory when the
 //      neighbour element is in the tile, else from global memory / L2), and accumulates into
 //      the shared right-hand side;
-//   4. node-parallel stage update with coalesced global reads/writes.
+//   4. node-parallel stage update with coalesced global reads/writes (2D FP64: fused into the
+//      y-line pass instead, each thread updating the nodes of its line).
 // The grid is persistent: CTAs loop over the tiles of every solve of the launch.
 #pragma once
 
@@ -179,6 +180,38 @@ __device__ __forceinline__ void contract_even_odd(const real (&f)[N + 1], real (
   }
 }
 
+// Quotient in the kernel's precision: IEEE division in FP64; in FP32 the reciprocal-based
+// __fdividef (2 ulp), well inside the FP32 path's tolerance and a fraction of the instructions.
+__device__ __forceinline__ double ratio(double a, double b) { return a / b; }
+__device__ __forceinline__ float ratio(float a, float b) { return __fdividef(a, b); }
+
+// A product rounded on its own: the compiler may not contract it into a following add.  Where a
+// flux is a plain product, letting the compiler choose would make the rounding depend on the
+// surrounding code, and the two thread mappings would no longer agree bit for bit.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+// Runge-Kutta stage update of one node (the Butcher tableau of Eq. (RK3)/(RK4)/(RK6) as the
+// StagePlan states it): r = L(U) / rhs_scale at the node, bb = U^n there (read unless the last
+// stage), aa = ACC there (read when it accumulates), g = its global index.
+template <int DIM, typename real>
+__device__ __forceinline__ void stage_update_node(const StageArgs<real>& args, const SolveRegs<DIM, real>& S, int si,
+                                                  const StagePlan& plan, long long g, real r, real bb, real aa) {
+  if (plan.acc_mode == 3) {
+    S.uout[g] = fma(S.bdt, r, aa);
+    return;
+  }
+  real o = fma(S.a_self, r, bb);
+  for (int j = 0; j < plan.nread; ++j) {
+    const real* kj = static_cast<const real*>(args.solves[si].buf[plan.kread[j]]);
+    o = fma(S.a_read(plan, j), kj[g], o);
+  }
+  S.uout[g] = o;
+  if (plan.acc_mode == 1) S.acc[g] = fma(S.bdt, r, bb);
+  else if (plan.acc_mode == 2) S.acc[g] = fma(S.bdt, r, aa);
+  if (S.kw) S.kw[g] = r;
+}
+
 // Where a line's two neighbour traces come from (element indices fit in 32 bits, checked at
 // creation): the periodic neighbours along axis a, or a partition halo on a partition boundary.
 struct LineTrace {
@@ -281,6 +314,12 @@ __global__ void stage_kernel(const StageArgs<real> args) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
   constexpr bool EARLY = DIM <= 2 && !FF;
+  // 2D FP64: the y-line threads own whole lines of finished right-hand side and apply the stage
+  // update to them directly (no shared round trip, one barrier less: 2D Euler 2.40 -> 2.28 ms per
+  // stage).  Elsewhere the extra registers cost more occupancy than the round trip does (measured:
+  // FP32 2D Euler 243 -> 260 us, float-float 93 -> 95 us, FP64 3D Euler no gain), so those keep the
+  // node-parallel update.
+  constexpr bool FUSED = DIM == 2 && !G::SLIM && !FF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const GroupHeader hdr = *args.hdr;
   const int epb = hdr.epb;
@@ -397,9 +436,11 @@ __global__ void stage_kernel(const StageArgs<real> args) {
       }
       __syncthreads();
     }
-    // ---- 3. volume + surface terms, axis by axis ----
+    // ---- 3. volume + surface terms, axis by axis (FUSED: the last axis applies the stage update
+    //         to the finished right-hand side of its line directly) ----
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
+      const bool last = FUSED && a == DIM - 1;
       const int el = tid / TPE;
       const int rem = tid - el * TPE;
       const int line = rem % L;
@@ -412,45 +453,69 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         const real vs = S.vs[a];
         const real qlo = S.qlo[a];
         const real qhi = S.qhi[a];
+        // operands of the fused update of variable v's nodes on this line: U^n and ACC where the
+        // plan reads them (loaded once the line's right-hand side is done: loaded earlier, they
+        // would hold registers through the contraction)
+        const long long gline = (e0 + el) * NPE + ubase;  // global node index of l = 0 (variable 0)
+        const int bline = el * NPE + ubase;               // the same in the staged U^n / ACC tiles
+        auto operands = [&](int v, real (&bb)[n], real (&aa)[n]) {
+          const long long g0 = v * vstride + gline;
+#pragma unroll
+          for (int l = 0; l < n; ++l) {
+            if (plan.acc_mode != 3)
+              bb[l] = plan.in == kUN ? sUe[v * epb * SPE + l * pstride]
+                                     : (G::SLIM ? S.un[g0 + l * ustride] : sB[v * epb * NPE + bline + l * ustride]);
+            if (plan.acc_mode >= 2) aa[l] = G::SLIM ? S.acc[g0 + l * ustride] : sA[v * epb * NPE + bline + l * ustride];
+          }
+        };
         // The right-hand side is kept divided by axis 0's scale (rhs_scale), so axis 0 needs no
         // multiply; a zero scale means advection with no velocity along this axis: no flux.
         if constexpr (EQ == 0) {
-         if (vs == real(0)) {
-          if (a == 0) {
+          real bb[n], aa[n];
+          if (vs == real(0)) {
+            // no flux along this axis: the right-hand side is what the other axes left
+            if (last) {
+              operands(0, bb, aa);
 #pragma unroll
-            for (int l = 0; l < n; ++l) sRe[l * pstride] = real(0);
-          }
-         } else {
-          // upwinding makes one of the two face terms vanish: its trace was not even loaded
-          const bool has_lo = qlo != real(0), has_hi = qhi != real(0);
-          real xlo = 0, xhi = 0;
-          if constexpr (EARLY) {
-            if (has_lo) xlo = xs_lo[a] >= 0 ? sU[xs_lo[a]] : xr_lo[a][0];
-            if (has_hi) xhi = xs_hi[a] >= 0 ? sU[xs_hi[a]] : xr_hi[a][0];
+              for (int l = 0; l < n; ++l)
+                stage_update_node(args, S, si, plan, gline + l * ustride, a == 0 ? real(0) : sRe[l * pstride], bb[l], aa[l]);
+            } else if (a == 0) {
+#pragma unroll
+              for (int l = 0; l < n; ++l) sRe[l * pstride] = real(0);
+            }
           } else {
-            const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), line, S.E0, S.E1, S.E2, nelem,
-                                              S.halo_lo[a] != nullptr, S.halo_hi[a] != nullptr);
-            if (has_lo)
-              xlo = t.lo_halo ? S.halo_lo[a][t.hoff]
-                              : (t.elo >= e0 && t.elo < e0 + cnt ? sU[(int)(t.elo - e0) * SPE + pbase + N * pstride]
-                                                                 : uin[t.elo * NPE + ubase + N * ustride]);
-            if (has_hi)
-              xhi = t.hi_halo ? S.halo_hi[a][t.hoff]
-                              : (t.ehi >= e0 && t.ehi < e0 + cnt ? sU[(int)(t.ehi - e0) * SPE + pbase]
-                                                                 : uin[t.ehi * NPE + ubase]);
-          }
-          real f[n], out[n];
+            // upwinding makes one of the two face terms vanish: its trace was not even loaded
+            const bool has_lo = qlo != real(0), has_hi = qhi != real(0);
+            real xlo = 0, xhi = 0;
+            if constexpr (EARLY) {
+              if (has_lo) xlo = xs_lo[a] >= 0 ? sU[xs_lo[a]] : xr_lo[a][0];
+              if (has_hi) xhi = xs_hi[a] >= 0 ? sU[xs_hi[a]] : xr_hi[a][0];
+            } else {
+              const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), line, S.E0, S.E1, S.E2, nelem,
+                                                S.halo_lo[a] != nullptr, S.halo_hi[a] != nullptr);
+              if (has_lo)
+                xlo = t.lo_halo ? S.halo_lo[a][t.hoff]
+                                : (t.elo >= e0 && t.elo < e0 + cnt ? sU[(int)(t.elo - e0) * SPE + pbase + N * pstride]
+                                                                   : uin[t.elo * NPE + ubase + N * ustride]);
+              if (has_hi)
+                xhi = t.hi_halo ? S.halo_hi[a][t.hoff]
+                                : (t.ehi >= e0 && t.ehi < e0 + cnt ? sU[(int)(t.ehi - e0) * SPE + pbase]
+                                                                   : uin[t.ehi * NPE + ubase]);
+            }
+            real f[n], out[n];
 #pragma unroll
-          for (int l = 0; l < n; ++l) f[l] = sUe[l * pstride];
-          contract_line<N, real, FF>(f, out, args);
+            for (int l = 0; l < n; ++l) f[l] = sUe[l * pstride];
+            contract_line<N, real, FF>(f, out, args);
+            if (last) operands(0, bb, aa);
 #pragma unroll
-          for (int l = 0; l < n; ++l) {
-            real r = (a == 0) ? out[l] : fma(vs, out[l], sRe[l * pstride]);
-            if (l == 0 && has_lo) r = fma(qlo, xlo - f[0], r);
-            if (l == N && has_hi) r = fma(qhi, f[N] - xhi, r);
-            sRe[l * pstride] = r;
+            for (int l = 0; l < n; ++l) {
+              real r = (a == 0) ? out[l] : fma(vs, out[l], sRe[l * pstride]);
+              if (l == 0 && has_lo) r = fma(qlo, xlo - f[0], r);
+              if (l == N && has_hi) r = fma(qhi, f[N] - xhi, r);
+              if (last) stage_update_node(args, S, si, plan, gline + l * ustride, r, bb[l], aa[l]);
+              else sRe[l * pstride] = r;
+            }
           }
-         }
         } else {
           // exterior traces: node N of the low neighbour, node 0 of the high neighbour
           real xlo[NV], xhi[NV];
@@ -482,7 +547,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           if constexpr (G::SLIM) {
             const real* sma = sUe + (1 + a) * epb * SPE;
 #pragma unroll
-            for (int l = 0; l < n; ++l) ua[l] = sma[l * pstride] / sUe[l * pstride];
+            for (int l = 0; l < n; ++l) ua[l] = ratio(sma[l * pstride], sUe[l * pstride]);
           } else {
             const real* sVa = sV + a * epb * SPE + el * SPE + pbase;
 #pragma unroll
@@ -490,14 +555,15 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           }
           // normal velocities and LLF alpha at both faces of the line
           const real un0 = ua[0], unN = ua[N];
-          const real unlo = xlo[1 + a] / xlo[0];
-          const real unhi = xhi[1 + a] / xhi[0];
+          const real unlo = ratio(xlo[1 + a], xlo[0]);
+          const real unhi = ratio(xhi[1 + a], xhi[0]);
           const real alo = fmax(fabs(unlo), fabs(un0)) + cs;
           const real ahi = fmax(fabs(unN), fabs(unhi)) + cs;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             if (VS && v != vsel) continue;
             const real* sUv = sUe + v * epb * SPE;
+            real bb[n], aa[n];
             real f[n], out[n];
             // flux component v along a (Eq. (eulerIso2d)): v = 0: m_a; v = 1 + b: m_b u_a
             // plus c^2 rho when b = a
@@ -510,7 +576,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               for (int l = 0; l < n; ++l) f[l] = fma(sUv[l * pstride], ua[l], c2 * sUe[l * pstride]);
             } else {
 #pragma unroll
-              for (int l = 0; l < n; ++l) f[l] = sUv[l * pstride] * ua[l];
+              for (int l = 0; l < n; ++l) f[l] = mul_rn(sUv[l * pstride], ua[l]);
             }
             contract_line<N, real, FF>(f, out, args);
             real fxlo, fxhi;
@@ -521,11 +587,13 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               fxlo = fma(xlo[v], unlo, c2 * xlo[0]);
               fxhi = fma(xhi[v], unhi, c2 * xhi[0]);
             } else {
-              fxlo = xlo[v] * unlo;
-              fxhi = xhi[v] * unhi;
+              fxlo = mul_rn(xlo[v], unlo);
+              fxhi = mul_rn(xhi[v], unhi);
             }
             const real u0 = sUv[0], uN = sUv[N * pstride];
             real* sRv = sRe + v * epb * SPE;
+            if (last) operands(v, bb, aa);
+            const long long gv = v * vstride + gline;
 #pragma unroll
             for (int l = 0; l < n; ++l) {
               real r = (a == 0) ? out[l] : fma(vs, out[l], sRv[l * pstride]);
@@ -533,20 +601,16 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               if (l == 0) r = fma(qlo, fma(-alo, u0 - xlo[v], fxlo - f[0]), r);
               // (F(U_N) - Fhat_hi) = 1/2 (F(U_N) - F(ext) + alpha (ext - U_N))
               if (l == N) r = fma(qhi, fma(ahi, xhi[v] - uN, f[N] - fxhi), r);
-              sRv[l * pstride] = r;
+              if (last) stage_update_node(args, S, si, plan, gv + l * ustride, r, bb[l], aa[l]);
+              else sRv[l * pstride] = r;
             }
           }
         }
       }
-      __syncthreads();
+      if (!last) __syncthreads();
     }
-    // ---- 4. Runge-Kutta stage update ----
-    {
-      const real a_self = S.a_self;
-      const real bdt = S.bdt;
-      real* __restrict__ uout = S.uout;
-      real* __restrict__ acc = S.acc;
-      real* __restrict__ kw = S.kw;
+    // ---- 4. Runge-Kutta stage update, node-parallel (unless fused into the last axis) ----
+    if constexpr (!FUSED) {
       const int total = cnt * NPE;
       // each thread owns up to B nodes per variable: all of their operands are loaded first, so
       // the loads are in flight together, then the results are computed and stored
@@ -568,28 +632,14 @@ __global__ void stage_kernel(const StageArgs<real> args) {
             const int s = el * SPE + G::pad(node);
             const long long g = goff + idx;
             rr[k] = sRv[s];
-            if (plan.acc_mode >= 2) aa[k] = G::SLIM ? acc[g] : sAv[idx];
+            if (plan.acc_mode >= 2) aa[k] = G::SLIM ? S.acc[g] : sAv[idx];
             if (plan.acc_mode != 3) bb[k] = plan.in == kUN ? sUv[s] : (G::SLIM ? S.un[g] : sBv[idx]);
           }
 #pragma unroll
           for (int k = 0; k < B; ++k) {
             const int idx = i0 + k * nthr;
             if (idx >= total) break;
-            const long long g = goff + idx;
-            const real r = rr[k];
-            if (plan.acc_mode == 3) {
-              uout[g] = fma(bdt, r, aa[k]);
-              continue;
-            }
-            real o = fma(a_self, r, bb[k]);
-            for (int j = 0; j < plan.nread; ++j) {
-              const real* kj = static_cast<const real*>(args.solves[si].buf[plan.kread[j]]);
-              o = fma(S.a_read(plan, j), kj[g], o);
-            }
-            uout[g] = o;
-            if (plan.acc_mode == 1) acc[g] = fma(bdt, r, bb[k]);
-            else if (plan.acc_mode == 2) acc[g] = fma(bdt, r, aa[k]);
-            if (kw) kw[g] = r;
+            stage_update_node(args, S, si, plan, goff + idx, rr[k], bb[k], aa[k]);
           }
         }
       }
