@@ -171,7 +171,9 @@ const char* ndg_last_error(void);
 /* Route the library's device allocations through caller-supplied functions (e.g. a framework's
  * caching allocator).  alloc(bytes, user, stream) returns a device pointer or NULL;
  * free(ptr, user, stream) releases it.  Pass NULLs to return to cudaMalloc/cudaFree.  Affects
- * allocations made after the call. */
+ * allocations made after the call.  Pointers must be aligned to 256 bytes, as cudaMalloc's are
+ * (the kernels access state arrays in 16-byte units); a less aligned one is handed back to free
+ * and the allocating call fails with NDG_ECUDA. */
 typedef void* (*ndg_alloc_fn)(size_t bytes, void* user, void* stream);
 typedef void (*ndg_free_fn)(void* ptr, void* user, void* stream);
 int ndg_set_allocator(ndg_alloc_fn alloc, ndg_free_fn free_fn, void* user);

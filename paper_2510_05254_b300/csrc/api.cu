@@ -2,6 +2,8 @@
 // batching of several solves into one graph per RK step, and the tile-size autotuner.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -132,6 +134,12 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream) {
   if (a) {
     *p = a(bytes, user, (void*)stream);
     if (!*p) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(*p) & 255) {
+      // the kernels access state arrays 16 bytes at a time: insist on cudaMalloc's alignment
+      if (f) f(*p, user, (void*)stream);
+      *p = nullptr;
+      return cudaErrorInvalidValue;
+    }
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     g_hooked[*p] = {f, user};
     return cudaSuccess;

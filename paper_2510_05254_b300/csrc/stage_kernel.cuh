@@ -147,6 +147,10 @@ __device__ __forceinline__ void cp_async_elem(real* smem_dst, const real* gmem_s
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
 
 template <int N, typename real>
 __device__ __forceinline__ void contract_even_odd(const real (&f)[N + 1], real (&out)[N + 1],
@@ -212,6 +216,42 @@ __device__ __forceinline__ void stage_update_node(const StageArgs<real>& args, c
   if (S.kw) S.kw[g] = r;
 }
 
+// The update of four consecutive nodes g .. g + 3 (16-byte aligned in every array), FP32: r and
+// the stage input (U^n at the first stage) read as float4 from shared memory, U^n / ACC as float4
+// from global memory; the same arithmetic as stage_update_node, node by node.
+template <int DIM>
+__device__ __forceinline__ void stage_update_quad(const StageArgs<float>& args, const SolveRegs<DIM, float>& S, int si,
+                                                  const StagePlan& plan, long long g, const float* sr, const float* su) {
+  const float4 r = *reinterpret_cast<const float4*>(sr);
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f), a = b;
+  if (plan.acc_mode >= 2) a = __ldg(reinterpret_cast<const float4*>(S.acc + g));
+  if (plan.acc_mode != 3)
+    b = plan.in == kUN ? *reinterpret_cast<const float4*>(su) : __ldg(reinterpret_cast<const float4*>(S.un + g));
+  if (plan.acc_mode == 3) {
+    *reinterpret_cast<float4*>(S.uout + g) =
+        make_float4(fmaf(S.bdt, r.x, a.x), fmaf(S.bdt, r.y, a.y), fmaf(S.bdt, r.z, a.z), fmaf(S.bdt, r.w, a.w));
+    return;
+  }
+  if (plan.nread > 0) {  // stored slopes (RK6): node by node
+    const float rr[4] = {r.x, r.y, r.z, r.w}, bb[4] = {b.x, b.y, b.z, b.w}, aa[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) stage_update_node(args, S, si, plan, g + k, rr[k], bb[k], aa[k]);
+    return;
+  }
+  *reinterpret_cast<float4*>(S.uout + g) =
+      make_float4(fmaf(S.a_self, r.x, b.x), fmaf(S.a_self, r.y, b.y), fmaf(S.a_self, r.z, b.z), fmaf(S.a_self, r.w, b.w));
+  if (plan.acc_mode == 1)
+    *reinterpret_cast<float4*>(S.acc + g) =
+        make_float4(fmaf(S.bdt, r.x, b.x), fmaf(S.bdt, r.y, b.y), fmaf(S.bdt, r.z, b.z), fmaf(S.bdt, r.w, b.w));
+  else if (plan.acc_mode == 2)
+    *reinterpret_cast<float4*>(S.acc + g) =
+        make_float4(fmaf(S.bdt, r.x, a.x), fmaf(S.bdt, r.y, a.y), fmaf(S.bdt, r.z, a.z), fmaf(S.bdt, r.w, a.w));
+  if (S.kw) *reinterpret_cast<float4*>(S.kw + g) = r;
+}
+template <int DIM>
+__device__ __forceinline__ void stage_update_quad(const StageArgs<double>&, const SolveRegs<DIM, double>&, int,
+                                                  const StagePlan&, long long, const double*, const double*) {}
+
 // Where a line's two neighbour traces come from (element indices fit in 32 bits, checked at
 // creation): the periodic neighbours along axis a, or a partition halo on a partition boundary.
 struct LineTrace {
@@ -252,16 +292,48 @@ __device__ __forceinline__ LineTrace line_trace(int a, unsigned eu, int line, un
 }
 
 // Padded shared-memory base / stride and unpadded node base / stride of line `line` along axis a.
-template <int n>
+// (x-lines in shared memory start RS slots apart: RS = n + 1, or a multiple of 4 for 16-byte access)
+template <int n, int RS>
 __device__ __forceinline__ void line_geometry(int a, int line, int& pbase, int& pstride, int& ubase, int& ustride) {
   if (a == 0) {
-    pbase = (n + 1) * line; pstride = 1; ubase = n * line; ustride = 1;
+    pbase = RS * line; pstride = 1; ubase = n * line; ustride = 1;
   } else if (a == 1) {
     const int i = line % n, k = line / n;
-    pbase = i + (n + 1) * n * k; pstride = n + 1; ubase = i + n * n * k; ustride = n;
+    pbase = i + RS * n * k; pstride = RS; ubase = i + n * n * k; ustride = n;
   } else {
-    pbase = line % n + (n + 1) * (line / n); pstride = (n + 1) * n; ubase = line; ustride = n * n;
+    pbase = line % n + RS * (line / n); pstride = RS * n; ubase = line; ustride = n * n;
   }
+}
+
+// One line of n values from shared memory into registers (V: contiguous and 16-byte aligned,
+// read as float4), and back.
+template <int n, typename real>
+__device__ __forceinline__ void load_line(const real* p, int stride, bool V, real (&f)[n]) {
+  if constexpr (sizeof(real) == 4 && n % 4 == 0) {
+    if (V) {
+#pragma unroll
+      for (int c = 0; c < n / 4; ++c) {
+        const float4 q = reinterpret_cast<const float4*>(p)[c];
+        f[4 * c] = q.x; f[4 * c + 1] = q.y; f[4 * c + 2] = q.z; f[4 * c + 3] = q.w;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < n; ++l) f[l] = p[l * stride];
+}
+template <int n, typename real>
+__device__ __forceinline__ void store_line(real* p, int stride, bool V, const real (&f)[n]) {
+  if constexpr (sizeof(real) == 4 && n % 4 == 0) {
+    if (V) {
+#pragma unroll
+      for (int c = 0; c < n / 4; ++c)
+        reinterpret_cast<float4*>(p)[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < n; ++l) p[l * stride] = f[l];
 }
 
 // D along one line: FP64 / FP32 even-odd products, or (FF) the float-float version of the same,
@@ -290,7 +362,14 @@ struct StageGeom {
   static constexpr int L = ipow_c(n, DIM - 1);      // lines per element along one axis
   static constexpr int NPE = ipow_c(n, DIM);        // nodes per element
   static constexpr int NV = EQ == 0 ? 1 : DIM + 1;  // variables
-  static constexpr int SPE = (n + 1) * L;           // padded shared slots per element
+  // VEC (FP32 2D, n = 8 or 4): x-lines 16-byte aligned in shared memory, so the tile copy, the
+  // x-line passes and the stage update move four values per instruction.  Row stride RS: an odd
+  // number of 16-byte chunks, so eight threads reading eight rows' chunks hit distinct banks;
+  // element stride SPE = 8 (mod 32) banks for n = 8 (20 for n = 4), so a warp's y-lines in four
+  // (eight) elements do too.  Otherwise x-lines are padded by one slot (RS = n + 1).
+  static constexpr bool VEC = sizeof(real) == 4 && DIM == 2 && (n == 8 || n == 4);
+  static constexpr int RS = VEC ? (n == 8 ? 12 : 4) : n + 1;
+  static constexpr int SPE = VEC ? (n == 8 ? 104 : 20) : RS * L;  // shared slots per element
   // FP64 (arithmetic-bound) stages U^n and ACC in shared memory and keeps the Euler velocities
   // there; FP32 (memory-bound) keeps shared memory small for occupancy: U^n / ACC are
   // prefetched into L2 and read directly, velocities are recomputed per line.
@@ -302,7 +381,7 @@ struct StageGeom {
   static constexpr int NB = SLIM ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
   static constexpr int TPE = VS ? L * NV : L;
-  __device__ static __forceinline__ int pad(int node) { return node + node / n; }
+  __device__ static __forceinline__ int pad(int node) { return (node / n) * RS + node % n; }
 };
 
 // VS = false: a thread owns a line for every variable (fewest FP64 operations: the wave speeds
@@ -353,9 +432,19 @@ __global__ void stage_kernel(const StageArgs<real> args) {
       for (int v = 0; v < NV; ++v) {
         const real* src = uin + v * vstride + e0 * NPE;
         real* dst = sU + v * epb * SPE;
-        for (int idx = tid; idx < total; idx += nthr) {
-          const int el = idx / NPE, node = idx - el * NPE;
-          cp_async_elem(dst + el * SPE + G::pad(node), src + idx);
+        if constexpr (G::VEC) {
+          // 16-byte copies: chunk q = 4 consecutive nodes of one x-line
+          constexpr int C = n / 4;
+          for (int q = tid; q < total / 4; q += nthr) {
+            const int row = q / C, c = q - row * C;
+            const int el = row / L, r = row - el * L;
+            cp_async_16(dst + el * SPE + r * G::RS + 4 * c, src + 4 * q);
+          }
+        } else {
+          for (int idx = tid; idx < total; idx += nthr) {
+            const int el = idx / NPE, node = idx - el * NPE;
+            cp_async_elem(dst + el * SPE + G::pad(node), src + idx);
+          }
         }
         if constexpr (G::SLIM) {
           // start the update's reads now: one L2 prefetch per 128-byte line of U^n / ACC
@@ -391,7 +480,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
       for (int a = 0; a < DIM; ++a) {
         xs_lo[a] = xs_hi[a] = -1;
         int pbase, pstride, ubase, ustride;
-        line_geometry<n>(a, line_t, pbase, pstride, ubase, ustride);
+        line_geometry<n, G::RS>(a, line_t, pbase, pstride, ubase, ustride);
         const LineTrace t = line_trace<L>(a, eu, line_t, S.E0, S.E1, S.E2, nelem, S.halo_lo[a] != nullptr,
                                           S.halo_hi[a] != nullptr);
         // advection: no flux along a zero-velocity axis, and upwinding zeroes one face
@@ -441,13 +530,14 @@ __global__ void stage_kernel(const StageArgs<real> args) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const bool last = FUSED && a == DIM - 1;
+      const bool VX = G::VEC && a == 0;  // x-lines contiguous and 16-byte aligned: float4 access
       const int el = tid / TPE;
       const int rem = tid - el * TPE;
       const int line = rem % L;
       const int vsel = rem / L;  // the variable this thread owns (VS), else 0
       if (el < cnt) {
         int pbase, pstride, ubase, ustride;
-        line_geometry<n>(a, line, pbase, pstride, ubase, ustride);
+        line_geometry<n, G::RS>(a, line, pbase, pstride, ubase, ustride);
         const real* sUe = sU + el * SPE + pbase;
         real* sRe = sR + el * SPE + pbase;
         const real vs = S.vs[a];
@@ -502,9 +592,8 @@ __global__ void stage_kernel(const StageArgs<real> args) {
                                 : (t.ehi >= e0 && t.ehi < e0 + cnt ? sU[(int)(t.ehi - e0) * SPE + pbase]
                                                                    : uin[t.ehi * NPE + ubase]);
             }
-            real f[n], out[n];
-#pragma unroll
-            for (int l = 0; l < n; ++l) f[l] = sUe[l * pstride];
+            real f[n], out[n], rr[n];
+            load_line<n>(sUe, pstride, VX, f);
             contract_line<N, real, FF>(f, out, args);
             if (last) operands(0, bb, aa);
 #pragma unroll
@@ -513,8 +602,9 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               if (l == 0 && has_lo) r = fma(qlo, xlo - f[0], r);
               if (l == N && has_hi) r = fma(qhi, f[N] - xhi, r);
               if (last) stage_update_node(args, S, si, plan, gline + l * ustride, r, bb[l], aa[l]);
-              else sRe[l * pstride] = r;
+              else rr[l] = r;
             }
+            if (!last) store_line<n>(sRe, pstride, VX, rr);
           }
         } else {
           // exterior traces: node N of the low neighbour, node 0 of the high neighbour
@@ -544,10 +634,12 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           const real cs = S.c;
           // velocity u_a along the line: from shared memory (FP64) or recomputed (FP32)
           real ua[n];
+          real rho[n], ma[n];  // FP32: the density and m_a lines, kept for the fluxes below
           if constexpr (G::SLIM) {
-            const real* sma = sUe + (1 + a) * epb * SPE;
+            load_line<n>(sUe, pstride, VX, rho);
+            load_line<n>(sUe + (1 + a) * epb * SPE, pstride, VX, ma);
 #pragma unroll
-            for (int l = 0; l < n; ++l) ua[l] = ratio(sma[l * pstride], sUe[l * pstride]);
+            for (int l = 0; l < n; ++l) ua[l] = ratio(ma[l], rho[l]);
           } else {
             const real* sVa = sV + a * epb * SPE + el * SPE + pbase;
 #pragma unroll
@@ -564,10 +656,27 @@ __global__ void stage_kernel(const StageArgs<real> args) {
             if (VS && v != vsel) continue;
             const real* sUv = sUe + v * epb * SPE;
             real bb[n], aa[n];
-            real f[n], out[n];
+            real f[n], out[n], rr[n];
+            real u0, uN;
             // flux component v along a (Eq. (eulerIso2d)): v = 0: m_a; v = 1 + b: m_b u_a
             // plus c^2 rho when b = a
-            if (v == 0) {
+            if constexpr (G::SLIM) {
+              if (v == 0) {
+#pragma unroll
+                for (int l = 0; l < n; ++l) f[l] = ma[l];
+                u0 = rho[0], uN = rho[N];
+              } else if (v == 1 + a) {
+#pragma unroll
+                for (int l = 0; l < n; ++l) f[l] = fma(ma[l], ua[l], c2 * rho[l]);
+                u0 = ma[0], uN = ma[N];
+              } else {
+                real mb[n];
+                load_line<n>(sUv, pstride, VX, mb);
+#pragma unroll
+                for (int l = 0; l < n; ++l) f[l] = mul_rn(mb[l], ua[l]);
+                u0 = mb[0], uN = mb[N];
+              }
+            } else if (v == 0) {
               const real* sm = sUe + (1 + a) * epb * SPE;
 #pragma unroll
               for (int l = 0; l < n; ++l) f[l] = sm[l * pstride];
@@ -590,7 +699,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               fxlo = mul_rn(xlo[v], unlo);
               fxhi = mul_rn(xhi[v], unhi);
             }
-            const real u0 = sUv[0], uN = sUv[N * pstride];
+            if constexpr (!G::SLIM) u0 = sUv[0], uN = sUv[N * pstride];
             real* sRv = sRe + v * epb * SPE;
             if (last) operands(v, bb, aa);
             const long long gv = v * vstride + gline;
@@ -602,15 +711,30 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               // (F(U_N) - Fhat_hi) = 1/2 (F(U_N) - F(ext) + alpha (ext - U_N))
               if (l == N) r = fma(qhi, fma(ahi, xhi[v] - uN, f[N] - fxhi), r);
               if (last) stage_update_node(args, S, si, plan, gv + l * ustride, r, bb[l], aa[l]);
-              else sRv[l * pstride] = r;
+              else rr[l] = r;
             }
+            if (!last) store_line<n>(sRv, pstride, VX, rr);
           }
         }
       }
       if (!last) __syncthreads();
     }
     // ---- 4. Runge-Kutta stage update, node-parallel (unless fused into the last axis) ----
-    if constexpr (!FUSED) {
+    if constexpr (G::VEC) {
+      // four consecutive nodes (every state array is 256-byte aligned: the allocation paths check) of one x-line per step: float4 shared reads and global accesses
+      const int quads = cnt * NPE / 4;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const real* sRv = sR + v * epb * SPE;
+        const real* sUv = sU + v * epb * SPE;
+        const long long goff = v * vstride + e0 * NPE;
+        for (int q = tid; q < quads; q += nthr) {
+          const int el = q / (NPE / 4), node = 4 * (q - el * (NPE / 4));
+          const int sl = el * SPE + (node / n) * G::RS + node % n;
+          stage_update_quad(args, S, si, plan, goff + 4 * q, sRv + sl, sUv + sl);
+        }
+      }
+    } else if constexpr (!FUSED) {
       const int total = cnt * NPE;
       // each thread owns up to B nodes per variable: all of their operands are loaded first, so
       // the loads are in flight together, then the results are computed and stored
