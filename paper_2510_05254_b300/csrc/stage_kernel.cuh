@@ -305,11 +305,11 @@ __device__ __forceinline__ void line_geometry(int a, int line, int& pbase, int& 
   }
 }
 
-// One line of n values from shared memory into registers (V: contiguous and 16-byte aligned,
-// read as float4), and back.
-template <int n, typename real>
+// One line of n values from shared memory into registers and back.  W > 1 (FP32 only): the line
+// is contiguous and 4W-byte aligned and moves as float2 / float4; V switches it on per call.
+template <int n, int W, typename real>
 __device__ __forceinline__ void load_line(const real* p, int stride, bool V, real (&f)[n]) {
-  if constexpr (sizeof(real) == 4 && n % 4 == 0) {
+  if constexpr (sizeof(real) == 4 && W == 4 && n % 4 == 0) {
     if (V) {
 #pragma unroll
       for (int c = 0; c < n / 4; ++c) {
@@ -318,17 +318,32 @@ __device__ __forceinline__ void load_line(const real* p, int stride, bool V, rea
       }
       return;
     }
+  } else if constexpr (sizeof(real) == 4 && W == 2 && n % 2 == 0) {
+    if (V) {
+#pragma unroll
+      for (int c = 0; c < n / 2; ++c) {
+        const float2 q = reinterpret_cast<const float2*>(p)[c];
+        f[2 * c] = q.x; f[2 * c + 1] = q.y;
+      }
+      return;
+    }
   }
 #pragma unroll
   for (int l = 0; l < n; ++l) f[l] = p[l * stride];
 }
-template <int n, typename real>
+template <int n, int W, typename real>
 __device__ __forceinline__ void store_line(real* p, int stride, bool V, const real (&f)[n]) {
-  if constexpr (sizeof(real) == 4 && n % 4 == 0) {
+  if constexpr (sizeof(real) == 4 && W == 4 && n % 4 == 0) {
     if (V) {
 #pragma unroll
       for (int c = 0; c < n / 4; ++c)
         reinterpret_cast<float4*>(p)[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
+      return;
+    }
+  } else if constexpr (sizeof(real) == 4 && W == 2 && n % 2 == 0) {
+    if (V) {
+#pragma unroll
+      for (int c = 0; c < n / 2; ++c) reinterpret_cast<float2*>(p)[c] = make_float2(f[2 * c], f[2 * c + 1]);
       return;
     }
   }
@@ -367,8 +382,14 @@ struct StageGeom {
   // number of 16-byte chunks, so eight threads reading eight rows' chunks hit distinct banks;
   // element stride SPE = 8 (mod 32) banks for n = 8 (20 for n = 4), so a warp's y-lines in four
   // (eight) elements do too.  Otherwise x-lines are padded by one slot (RS = n + 1).
+  // DENSE (FP32 3D, n = 6): no padding at all -- x-lines read as float2 are conflict-free and y/z
+  // lines conflict less than with padding -- so the tile copy and the update are plain 16-byte
+  // streams over contiguous memory.
   static constexpr bool VEC = sizeof(real) == 4 && DIM == 2 && (n == 8 || n == 4);
-  static constexpr int RS = VEC ? (n == 8 ? 12 : 4) : n + 1;
+  static constexpr bool DENSE = sizeof(real) == 4 && DIM == 3 && n == 6;
+  static constexpr bool QUAD = VEC || DENSE;  // copy and update in 16-byte units
+  static constexpr int XW = VEC ? 4 : (DENSE ? 2 : 1);  // x-line access width (floats)
+  static constexpr int RS = VEC ? (n == 8 ? 12 : 4) : (DENSE ? n : n + 1);
   static constexpr int SPE = VEC ? (n == 8 ? 104 : 20) : RS * L;  // shared slots per element
   // FP64 (arithmetic-bound) stages U^n and ACC in shared memory and keeps the Euler velocities
   // there; FP32 (memory-bound) keeps shared memory small for occupancy: U^n / ACC are
@@ -382,6 +403,12 @@ struct StageGeom {
   // threads per element: one per line, or (VS) one per line and variable
   static constexpr int TPE = VS ? L * NV : L;
   __device__ static __forceinline__ int pad(int node) { return (node / n) * RS + node % n; }
+  // shared slot of the first of four consecutive nodes (QUAD: quad q of the tile)
+  __device__ static __forceinline__ int quad_slot(int q) {
+    if constexpr (DENSE) return 4 * q;
+    const int el = q / (NPE / 4), node = 4 * (q - el * (NPE / 4));
+    return el * SPE + (node / n) * RS + node % n;
+  }
 };
 
 // VS = false: a thread owns a line for every variable (fewest FP64 operations: the wave speeds
@@ -440,6 +467,8 @@ __global__ void stage_kernel(const StageArgs<real> args) {
             const int el = row / L, r = row - el * L;
             cp_async_16(dst + el * SPE + r * G::RS + 4 * c, src + 4 * q);
           }
+        } else if constexpr (G::DENSE) {
+          for (int q = tid; q < total / 4; q += nthr) cp_async_16(dst + 4 * q, src + 4 * q);
         } else {
           for (int idx = tid; idx < total; idx += nthr) {
             const int el = idx / NPE, node = idx - el * NPE;
@@ -530,7 +559,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const bool last = FUSED && a == DIM - 1;
-      const bool VX = G::VEC && a == 0;  // x-lines contiguous and 16-byte aligned: float4 access
+      const bool VX = G::XW > 1 && a == 0;  // x-lines contiguous and aligned: float2 / float4 access
       const int el = tid / TPE;
       const int rem = tid - el * TPE;
       const int line = rem % L;
@@ -593,7 +622,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
                                                                    : uin[t.ehi * NPE + ubase]);
             }
             real f[n], out[n], rr[n];
-            load_line<n>(sUe, pstride, VX, f);
+            load_line<n, G::XW>(sUe, pstride, VX, f);
             contract_line<N, real, FF>(f, out, args);
             if (last) operands(0, bb, aa);
 #pragma unroll
@@ -604,7 +633,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               if (last) stage_update_node(args, S, si, plan, gline + l * ustride, r, bb[l], aa[l]);
               else rr[l] = r;
             }
-            if (!last) store_line<n>(sRe, pstride, VX, rr);
+            if (!last) store_line<n, G::XW>(sRe, pstride, VX, rr);
           }
         } else {
           // exterior traces: node N of the low neighbour, node 0 of the high neighbour
@@ -636,8 +665,8 @@ __global__ void stage_kernel(const StageArgs<real> args) {
           real ua[n];
           real rho[n], ma[n];  // FP32: the density and m_a lines, kept for the fluxes below
           if constexpr (G::SLIM) {
-            load_line<n>(sUe, pstride, VX, rho);
-            load_line<n>(sUe + (1 + a) * epb * SPE, pstride, VX, ma);
+            load_line<n, G::XW>(sUe, pstride, VX, rho);
+            load_line<n, G::XW>(sUe + (1 + a) * epb * SPE, pstride, VX, ma);
 #pragma unroll
             for (int l = 0; l < n; ++l) ua[l] = ratio(ma[l], rho[l]);
           } else {
@@ -671,7 +700,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
                 u0 = ma[0], uN = ma[N];
               } else {
                 real mb[n];
-                load_line<n>(sUv, pstride, VX, mb);
+                load_line<n, G::XW>(sUv, pstride, VX, mb);
 #pragma unroll
                 for (int l = 0; l < n; ++l) f[l] = mul_rn(mb[l], ua[l]);
                 u0 = mb[0], uN = mb[N];
@@ -713,15 +742,16 @@ __global__ void stage_kernel(const StageArgs<real> args) {
               if (last) stage_update_node(args, S, si, plan, gv + l * ustride, r, bb[l], aa[l]);
               else rr[l] = r;
             }
-            if (!last) store_line<n>(sRv, pstride, VX, rr);
+            if (!last) store_line<n, G::XW>(sRv, pstride, VX, rr);
           }
         }
       }
       if (!last) __syncthreads();
     }
     // ---- 4. Runge-Kutta stage update, node-parallel (unless fused into the last axis) ----
-    if constexpr (G::VEC) {
-      // four consecutive nodes (every state array is 256-byte aligned: the allocation paths check) of one x-line per step: float4 shared reads and global accesses
+    if constexpr (G::QUAD) {
+      // four consecutive nodes of one x-line per step: float4 shared reads and global accesses
+      // (every state array is 256-byte aligned: the allocation paths check)
       const int quads = cnt * NPE / 4;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -729,8 +759,7 @@ __global__ void stage_kernel(const StageArgs<real> args) {
         const real* sUv = sU + v * epb * SPE;
         const long long goff = v * vstride + e0 * NPE;
         for (int q = tid; q < quads; q += nthr) {
-          const int el = q / (NPE / 4), node = 4 * (q - el * (NPE / 4));
-          const int sl = el * SPE + (node / n) * G::RS + node % n;
+          const int sl = G::quad_slot(q);
           stage_update_quad(args, S, si, plan, goff + 4 * q, sRv + sl, sUv + sl);
         }
       }
