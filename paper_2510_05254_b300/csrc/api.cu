@@ -930,7 +930,7 @@ int ndg_autotune(ndg_ctx* c, int rk, int* best_epb, double* best_ms) {
   const long long s0 = c->steps;
   // a tiny step keeps the state bounded while timing
   double dt = 1e-6;
-  const int cands[] = {1, 2, 4, 8, 16, 32, 64};
+  const int cands[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
   TileConfig best = c->tile;
   double best_t = 1e300;
   cudaEvent_t a, b;

@@ -134,8 +134,11 @@ def test_tile_size_does_not_change_results_bitwise(epb):
     assert np.array_equal(got, s2.get_state())
 
 
-@pytest.mark.parametrize("dim,N,E,eq", [(1, 3, (11,), 0), (2, 7, (6, 5), 0), (2, 5, (5, 4), 1),
-                                        (3, 3, (3, 3, 2), 1)])
+# (2, 7) and (2, 3) take the FP32 kernel's 16-byte-aligned 2D layout, (3, 5) its unpadded 3D
+# layout with shared trace slots; the others the padded layout
+@pytest.mark.parametrize("dim,N,E,eq", [(1, 3, (11,), 0), (2, 7, (6, 5), 0), (2, 7, (6, 5), 1), (2, 5, (5, 4), 1),
+                                        (2, 3, (7, 5), 1), (3, 3, (3, 3, 2), 1), (3, 5, (3, 2, 3), 1),
+                                        (3, 5, (2, 3, 3), 0)])
 def test_fp32_path(dim, N, E, eq):
     p, s = make(dim, N, E, eq, dtype="f32", epb=4)
     U = initial(p)
@@ -147,6 +150,13 @@ def test_fp32_path(dim, N, E, eq):
     s.step(dt, 9, 4)
     ref = orc.step(p, ref, dt, 9, 4)
     assert rel_l2(s.get_state(), ref) < 10 * F32_TOL
+    # the other schemes' stage plans (RK3: ACC accumulation; RK6: stored slopes), ragged tiles
+    for rk in (3, 6):
+        p3, s3 = make(dim, N, E, eq, dtype="f32", epb=3)
+        s3.set_state(U)
+        s3.step(dt, 2, rk)
+        ref = orc.step(p3, U.astype(np.float32).astype(np.float64), dt, 2, rk)
+        assert rel_l2(s3.get_state(), ref) < 2 * F32_TOL
 
 
 def test_config1_one_revolution_matches_oracle():
@@ -380,7 +390,8 @@ def test_torch_allocator_hook():
 
 @pytest.mark.parametrize("kernel", [nat.NDG_KERNEL_LINE, nat.NDG_KERNEL_LINE_VAR])
 @pytest.mark.parametrize("dim,N,E,eq", [(1, 4, (7,), 1), (2, 7, (5, 3), 0), (2, 6, (4, 3), 1), (2, 3, (6, 5), 1),
-                                        (3, 2, (3, 2, 3), 1), (3, 5, (2, 2, 3), 0), (3, 3, (2, 3, 2), 1)])
+                                        (3, 2, (3, 2, 3), 1), (3, 5, (2, 2, 3), 0), (3, 3, (2, 3, 2), 1),
+                                        (3, 5, (2, 3, 2), 1), (2, 7, (5, 4), 1)])
 def test_both_kernel_mappings(kernel, dim, N, E, eq):
     """Thread per line (all variables) and thread per (line, variable): FP64 within 1e-12 per
     step (RK4 and RK6), FP32 within its tolerance, with tiles that leave a ragged end; and the
