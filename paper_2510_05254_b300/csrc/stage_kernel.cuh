@@ -421,7 +421,7 @@ template <int DIM, typename real>
 constexpr int stage_reg_cap() { return (DIM == 3 && sizeof(real) == 4) ? 96 : 255; }
 
 template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
-__global__ void __maxnreg__(stage_reg_cap<DIM, real>()) stage_kernel(const StageArgs<real> args) {
+__global__ void __maxnreg__((stage_reg_cap<DIM, real>())) stage_kernel(const StageArgs<real> args) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
   constexpr bool EARLY = DIM <= 2 && !FF;
