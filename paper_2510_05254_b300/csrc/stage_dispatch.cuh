@@ -77,7 +77,7 @@ void shape_of(int variant, int epb, int* threads, size_t* smem) {
 
 template <int N, int EQ, bool VS>
 void launch_kernel(int grid, int threads, size_t smem, void* stream, const StageArgs<NDG_REAL>& args) {
-  stage_kernel<NDG_DIM, N, EQ, NDG_REAL, VS, NDG_FF><<<grid, threads, smem, (cudaStream_t)stream>>>(args);
+  stage_entry<NDG_DIM, N, EQ, NDG_REAL, VS, NDG_FF>()<<<grid, threads, smem, (cudaStream_t)stream>>>(args);
 }
 
 template <int N, int EQ>
@@ -100,8 +100,8 @@ int launch_one(int variant, int grid, int epb, const SolveDesc* solves, const Gr
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaFuncAttributes fa{};
-    if (variant == kLineVarKernel) cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF>);
-    else cudaFuncGetAttributes(&fa, stage_kernel<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF>);
+    if (variant == kLineVarKernel) cudaFuncGetAttributes(&fa, stage_entry<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF>());
+    else cudaFuncGetAttributes(&fa, stage_entry<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF>());
     launch_error_detail(grid, threads, smem, fa.maxThreadsPerBlock, fa.numRegs, fa.localSizeBytes,
                         fa.maxDynamicSharedSizeBytes);
   }
@@ -129,8 +129,8 @@ int prepare_one(int variant, int epb, int* max_blocks) {
   shape_of<N, EQ>(variant, epb, &threads, &smem);
   if (threads > 1024 || threads < 1) return (int)cudaErrorInvalidConfiguration;
   if (variant == kLineVarKernel)
-    return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF>, threads, smem, max_blocks);
-  return occupancy(stage_kernel<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF>, threads, smem, max_blocks);
+    return occupancy(stage_entry<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF>(), threads, smem, max_blocks);
+  return occupancy(stage_entry<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF>(), threads, smem, max_blocks);
 }
 
 template <int N, int EQ>

@@ -415,13 +415,8 @@ struct StageGeom {
 // of the face flux are computed once per line).  VS = true: a thread owns one (line, variable)
 // pair, so an Euler CTA has nvar times more threads for the same shared memory; the operations
 // per variable are the same, in the same order, so the results are bitwise identical.
-// Register budget per thread: FP32 3D is capped at 96 (no spills) -- one more CTA per SM than the
-// compiler's 106 allows (FP32 3D Euler 1.34 -> 1.24 ms per stage); others take what they need.
-template <int DIM, typename real>
-constexpr int stage_reg_cap() { return (DIM == 3 && sizeof(real) == 4) ? 96 : 255; }
-
 template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
-__global__ void __maxnreg__((stage_reg_cap<DIM, real>())) stage_kernel(const StageArgs<real> args) {
+__device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
   constexpr bool EARLY = DIM <= 2 && !FF;
@@ -804,6 +799,24 @@ __global__ void __maxnreg__((stage_reg_cap<DIM, real>())) stage_kernel(const Sta
     }
     __syncthreads();
   }
+}
+
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
+__global__ void stage_kernel(const StageArgs<real> args) {
+  stage_body<DIM, N, EQ, real, VS, FF>(args);
+}
+// The same with the register budget capped at 96 per thread (no spills), used for FP32 3D: one CTA
+// per SM more than the compiler's own choice of 106 allows (FP32 3D Euler 1.34 -> 1.24 ms per
+// stage).  A cap on the other classes would not be neutral: it changes the compiler's allocation.
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
+__global__ void __maxnreg__(96) stage_kernel_r96(const StageArgs<real> args) {
+  stage_body<DIM, N, EQ, real, VS, FF>(args);
+}
+// The entry point of a kernel class.
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
+constexpr auto stage_entry() {
+  if constexpr (DIM == 3 && sizeof(real) == 4) return &stage_kernel_r96<DIM, N, EQ, real, VS, FF>;
+  else return &stage_kernel<DIM, N, EQ, real, VS, FF>;
 }
 
 template <int DIM, int N, int EQ, typename real, bool VS>
