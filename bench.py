@@ -9,6 +9,10 @@ of every bench step.  FP64 is the headline; the FP32 variant and a mixed serving
 reported beside it; the FP64 CPU oracle (single thread, as it stands) gives the CPU baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-serving]
+                    [--no-workloads] [--workload adv2d|euler2d|euler3d] [--variants f64,f32,f64ff]
+
+Beside the headline, the line carries a table of the two isothermal Euler problems (2D 512^2 at
+degree 7, 3D 64^3 at degree 5): FP64 and FP32 ms per stage with their roofline fractions.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload ("replicas only":
 the solve is not partitioned across GPUs); value = total DOF-updates / max rank time.
@@ -59,6 +63,15 @@ def select_workload(name):
 FLOPS_PER_DOF = {"adv2d": 40.0, "euler2d": 48.0, "euler3d": 60.0}
 FLOPS_PER_DOF_STAGE = FLOPS_PER_DOF["adv2d"]
 PASSES_PER_STAGE = 4.0
+
+
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}\n")
+    sys.stderr.flush()
 
 
 def load_peaks():
@@ -217,7 +230,13 @@ def run_solver_timed(dtype, args, dev, pg, U0_host):
     U0 = torch.tensor(U0_host, device=f"cuda:{dev}", dtype=s.torch_dtype)
     s.set_state(U0)
     dt = s.stable_dt(CFL)
-    epb, _ = s.autotune(RK)  # the library's tile autotuner (state is restored bitwise)
+    if args.epb:  # a fixed tile (profiler captures of the tuned configuration)
+        s.close()
+        s = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype=dtype, device=dev, elems_per_block=args.epb)
+        s.set_state(U0)
+        epb = args.epb
+    else:
+        epb, _ = s.autotune(RK)  # the library's tile autotuner (state is restored bitwise)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
     from paper_2510_05254_b300 import native as nat
 
@@ -292,17 +311,17 @@ def run_serving(args, dev):
     reqs = serving.prepare(inputs.serving_stream(n, emax=args.serving_emax), nsteps=100)
     import torch
     budget = 120 << 30
+    log("serving inputs ready")
     pool_stats, _ = serving.run_pool(reqs, math.inf, budget)
     torch.cuda.synchronize(dev)
     serial_stats, _ = serving.run_serial(reqs, math.inf)
-    # the one-solve-at-a-time FP64 path: every request in FP64, one after another
-    reqs64 = serving.prepare([dict(r, dtype="f64") for r in inputs.serving_stream(n, emax=args.serving_emax)],
-                             nsteps=100)
-    serial64_stats, _ = serving.run_serial(reqs64, math.inf)
-    del reqs64
     # latency at a finite arrival rate: half of the pool's measured capacity
     rate = 0.5 * pool_stats["solves_per_s"]
     pool_rate_stats, _ = serving.run_pool(reqs, rate, budget)
+    # the one-solve-at-a-time FP64 path: every request in FP64, one after another
+    reqs = serving.as_fp64(reqs)
+    serial64_stats, _ = serving.run_serial(reqs, math.inf)
+    del reqs
     return {"workload": f"{n} independent 2D solves (advection / isothermal Euler 50/50, elements per axis "
                         f"log-uniform in [16,{args.serving_emax}], degree in {{3,5,7}}, FP64/FP32 50/50), "
                         "100 RK4 steps each, 120 GB budget",
@@ -310,6 +329,56 @@ def run_serving(args, dev):
                       "speedup_solves_per_s": pool_stats["solves_per_s"] / serial_stats["solves_per_s"],
                       "speedup_vs_f64_one_at_a_time": pool_stats["solves_per_s"] / serial64_stats["solves_per_s"]},
             "poisson_half_capacity": {"rate_per_s": rate, "pool": pool_rate_stats}}
+
+
+def run_workload_table(dev, peaks):
+    """The other two full-size problems (2D isothermal Euler 512^2 degree 7, 3D isothermal Euler
+    64^3 degree 5): ms per RK4 stage of the autotuned tile in FP64 and FP32, CUDA events around a
+    run of RK4 steps, with the FP64-pipe and HBM roofline fractions.  Their working sets (>= 0.8 GB
+    per array) are far larger than L2."""
+    import torch
+    from paper_2510_05254_b300 import inputs
+    from paper_2510_05254_b300.solver import Solver
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    p64 = fp64_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+    out = {}
+    for name, nsteps in (("euler2d", 25), ("euler3d", 5)):
+        dim, deg, el, eq, vel, _, desc = WORKLOADS[name]
+        row = {"workload": desc}
+        U0 = None
+        for dtype in ("f64", "f32"):
+            s = Solver(dim, deg, el, equation=eq, velocity=vel, dtype=dtype, device=dev)
+            if U0 is None:
+                X = s.node_coords()
+                U0 = np.ascontiguousarray(inputs.euler_shear(X) if dim == 2 else inputs.taylor_green(X))
+                del X
+            s.set_state(U0)
+            dt = s.stable_dt(CFL)
+            epb, _ = s.autotune(RK)
+            log(f"{name} {dtype} autotuned (epb {epb})")
+            n = nsteps if dtype == "f64" else 4 * nsteps
+            s.step(dt, 1, RK)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s.stream)
+            s.step(dt, n, RK)
+            b.record(s.stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / (n * STAGES)
+            r = {"ms_per_stage": ms, "dof_updates_per_s": s.ndof / (ms * 1e-3), "elems_per_block": epb,
+                 "mapping": "line" if s.kernel == 1 else "line_var"}
+            if dtype == "f64":
+                tf = FLOPS_PER_DOF[name] * s.ndof / (ms * 1e-3) / 1e12
+                r.update({"tflops": tf, "frac_fp64_peak": tf / p64})
+            else:
+                gbs = PASSES_PER_STAGE * 4 * s.ndof / (ms * 1e-3) / 1e9
+                r.update({"gbs": gbs, "frac_hbm": gbs / hbm})
+            row[dtype] = r
+            row["dof"] = s.ndof
+            s.close()
+        del U0
+        torch.cuda.empty_cache()
+        out[name] = row
+    return out
 
 
 def energy_block(r64, r32, work, t64_ms, t32_ms, rff=None, tff_ms=None):
@@ -335,9 +404,13 @@ def run_ours(args, world, rank, dev, pg):
     chosen = set(args.variants.split(","))
     skipped = {"total_ms": float("nan"), "stage_ms": float("nan"), "ndof": None, "clocks": None, "epb": None,
                "kernel": None, "l2_norm": None, "mass": None, "state_bytes": 0}
+    log("initial condition ready")
     r64 = run_solver_timed("f64", args, dev, pg, U0) if "f64" in chosen else dict(skipped)
+    log("f64 timed")
     r32 = run_solver_timed("f32", args, dev, pg, U0) if "f32" in chosen else dict(skipped)
+    log("f32 timed")
     rff = run_solver_timed("f64ff", args, dev, pg, U0) if "f64ff" in chosen else dict(skipped)
+    log("f64ff timed")
     for r in (r64, r32, rff):
         if r["ndof"] is None:
             r["ndof"] = next(x["ndof"] for x in (r64, r32, rff) if x["ndof"] is not None)
@@ -348,6 +421,7 @@ def run_ours(args, world, rank, dev, pg):
     value = world * work / (t64 * 1e-3)
     value32 = world * work / (t32 * 1e-3)
     e2e_s, nb = run_e2e(args, dev, U0) if "f64" in chosen else (float("nan"), 0)
+    log("e2e timed")
     e2e_s = max_over_ranks(pg, e2e_s, dev)
     # roofline of the dominant kernel (the fused stage kernel)
     clocks = r64["clocks"] or {}
@@ -396,8 +470,13 @@ def run_ours(args, world, rank, dev, pg):
         line["cpu_baseline"] = {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{args.cpu_steps} RK4 steps of the full 4.19M-DOF workload "
                                           f"({el:.1f} s, single-threaded FP64 oracle)"}
+    log("cpu baseline done")
+    if not args.no_workloads and args.workload == "adv2d":
+        line["workloads"] = run_workload_table(dev, peaks)
+        log("workload table done")
     if rank == 0 and not args.no_serving:
         line["serving"] = run_serving(args, dev)
+        log("serving done")
     return line
 
 
@@ -409,14 +488,26 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the 2D / 3D isothermal Euler table (FP64 and FP32 ms per stage)")
     ap.add_argument("--cpu-steps", type=int, default=15)
     ap.add_argument("--serving-solves", type=int, default=200)
     ap.add_argument("--serving-emax", type=int, default=512)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="adv2d")
+    ap.add_argument("--epb", type=int, default=0,
+                    help="elements per CTA tile instead of autotuning (profiler captures)")
+    ap.add_argument("--elems", type=int, default=0,
+                    help="elements per axis instead of the workload's (smaller cases for profiler captures)")
     ap.add_argument("--variants", default="f64,f32,f64ff",
                     help="precisions to time (comma list of f64, f32, f64ff); f64 is the headline")
     args = ap.parse_args()
     select_workload(args.workload)
+    if args.elems:
+        global ELEMS, WORKLOAD
+        ELEMS = (args.elems,) * DIM
+        WORKLOAD = WORKLOAD.split(",")[0] + f", {args.elems}^{DIM} elements (reduced for a profiler capture)"
+        args.no_cpu_baseline = True
+        args.no_workloads = True
     global FLOPS_PER_DOF_STAGE
     FLOPS_PER_DOF_STAGE = FLOPS_PER_DOF[args.workload]
     if args.workload != "adv2d":  # the roofline flop count and the CPU sample are the bench workload's

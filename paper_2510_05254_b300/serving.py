@@ -19,41 +19,32 @@ from . import native as nat
 CFL = 0.1
 
 
-def _coords(dim, degree, E):
-    """Node coordinates (dim, nelem, npe) on the unit box from the library's LGL nodes."""
-    xi, _ = nat.ndg_lgl(degree)
-    xi = np.asarray(xi)
-    n = degree + 1
-    axes = []
-    for a in range(dim):
-        h = 1.0 / E[a]
-        axes.append((np.arange(E[a])[:, None] * h + 0.5 * h * (xi[None, :] + 1.0)))  # (E, n)
-    if dim == 1:
-        return axes[0].reshape(1, E[0], n)
-    X = np.empty((2, E[1], E[0], n, n))
-    X[0] = axes[0][None, :, None, :]
-    X[1] = axes[1][:, None, :, None]
-    return X.reshape(2, E[0] * E[1], n * n)
-
-
 def prepare(requests, nsteps=100):
-    """Initial states and time steps of the serving workload (outside any timed region)."""
+    """Initial states and time steps of the serving workload (outside any timed region), from the
+    separable grid forms of the initial conditions (the same values as the pointwise ones)."""
     out = []
     for r in requests:
-        E = (r["elems"], r["elems"])
-        X = _coords(2, r["degree"], E)
+        E, N = r["elems"], r["degree"]
+        xi, _ = nat.ndg_lgl(N)
+        xi = np.asarray(xi)
+        h = 1.0 / E
+        x = (np.arange(E)[:, None] * h + 0.5 * h * (xi[None, :] + 1.0)).reshape(-1)
         if r["equation"] == 0:
-            U = inputs.gaussian_noise(X, seed=r["seed"])
+            U = inputs.grid_state("gaussian_noise", x, E, N + 1, r["seed"])
             lam = 1.0 + 0.5
         else:
-            U = inputs.euler_shear(X, seed=r["seed"])
+            U = inputs.grid_state("euler_shear", x, E, N + 1, r["seed"])
             lam = float(np.max(np.abs(U[1] / U[0]) + np.abs(U[2] / U[0]))) + 2.0
-        xi, _ = nat.ndg_lgl(r["degree"])
-        gap = min(xi[k + 1] - xi[k] for k in range(r["degree"]))
-        dt = CFL * (0.5 / r["elems"]) * gap / lam
+        gap = min(xi[k + 1] - xi[k] for k in range(N))
+        dt = CFL * (0.5 / E) * gap / lam
         U = np.ascontiguousarray(U, dtype=np.float64 if r["dtype"] == "f64" else np.float32)
         out.append(dict(r, U=U, dt=dt, nsteps=nsteps))
     return out
+
+
+def as_fp64(reqs):
+    """The same requests, every one in FP64 (states widened in place of a new draw)."""
+    return [dict(r, dtype="f64", U=np.ascontiguousarray(r["U"], dtype=np.float64)) for r in reqs]
 
 
 def _cfg(r):
