@@ -269,7 +269,8 @@ def run_solver_timed(dtype, args, dev, pg, U0_host):
     stage_ms = sum(a.elapsed_time(b) for a, b in inner) / (args.steps * NSTEPS * STAGES)
     out = {"total_ms": total_ms, "stage_ms": stage_ms, "ndof": s.ndof, "dt": dt, "clocks": clk.summary(), "epb": epb,
            "kernel": "line" if s.kernel == 1 else "line_var",
-           "l2_norm": nr.l2, "mass": nr.integral[0], "state_bytes": s.state_bytes}
+           "l2_norm": nr.l2, "mass": nr.integral[0], "state_bytes": s.state_bytes,
+           "final": s.get_state()}  # after NSTEPS steps from U0 (accuracy of the precisions)
     s.close()
     return out
 
@@ -318,6 +319,14 @@ def run_serving(args, dev):
     # latency at a finite arrival rate: half of the pool's measured capacity
     rate = 0.5 * pool_stats["solves_per_s"]
     pool_rate_stats, _ = serving.run_pool(reqs, rate, budget)
+    # and at a quarter of and at the full measured capacity (p50 / p99 against the arrival rate)
+    sweep = []
+    for frac in (0.25, 1.0):
+        st, _ = serving.run_pool(reqs, frac * pool_stats["solves_per_s"], budget)
+        sweep.append({"rate_per_s": frac * pool_stats["solves_per_s"], "fraction_of_capacity": frac,
+                      "solves_per_s": st["solves_per_s"], "p50_s": st["p50_s"], "p99_s": st["p99_s"]})
+    sweep.insert(1, {"rate_per_s": rate, "fraction_of_capacity": 0.5, "solves_per_s": pool_rate_stats["solves_per_s"],
+                     "p50_s": pool_rate_stats["p50_s"], "p99_s": pool_rate_stats["p99_s"]})
     # the one-solve-at-a-time FP64 path: every request in FP64, one after another
     reqs = serving.as_fp64(reqs)
     serial64_stats, _ = serving.run_serial(reqs, math.inf)
@@ -328,7 +337,8 @@ def run_serving(args, dev):
             "burst": {"pool": pool_stats, "one_at_a_time": serial_stats, "one_at_a_time_all_f64": serial64_stats,
                       "speedup_solves_per_s": pool_stats["solves_per_s"] / serial_stats["solves_per_s"],
                       "speedup_vs_f64_one_at_a_time": pool_stats["solves_per_s"] / serial64_stats["solves_per_s"]},
-            "poisson_half_capacity": {"rate_per_s": rate, "pool": pool_rate_stats}}
+            "poisson_half_capacity": {"rate_per_s": rate, "pool": pool_rate_stats},
+            "poisson_rate_sweep": sweep}
 
 
 def run_workload_table(dev, peaks):
@@ -346,6 +356,7 @@ def run_workload_table(dev, peaks):
         dim, deg, el, eq, vel, _, desc = WORKLOADS[name]
         row = {"workload": desc}
         U0 = None
+        finals = {}
         for dtype in ("f64", "f32"):
             s = Solver(dim, deg, el, equation=eq, velocity=vel, dtype=dtype, device=dev)
             if U0 is None:
@@ -356,7 +367,8 @@ def run_workload_table(dev, peaks):
             dt = s.stable_dt(CFL)
             epb, _ = s.autotune(RK)
             log(f"{name} {dtype} autotuned (epb {epb})")
-            n = nsteps if dtype == "f64" else 4 * nsteps
+            n = nsteps
+            s.set_state(U0)  # the autotuner restored it; start the timed run from U0 again
             s.step(dt, 1, RK)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(s.stream)
@@ -374,11 +386,21 @@ def run_workload_table(dev, peaks):
                 r.update({"gbs": gbs, "frac_hbm": gbs / hbm})
             row[dtype] = r
             row["dof"] = s.ndof
+            finals[dtype] = s.get_state()
             s.close()
-        del U0
+        row["accuracy_f32_vs_f64"] = dict(rel_err(finals["f32"], finals["f64"]), steps=nsteps + 1)
+        del U0, finals
         torch.cuda.empty_cache()
         out[name] = row
     return out
+
+
+def rel_err(a, ref):
+    """Relative L2 and Linf difference of two states (numpy, FP64 arithmetic)."""
+    d = np.asarray(a, dtype=np.float64) - np.asarray(ref, dtype=np.float64)
+    return {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+            "rel_linf": float(np.abs(d).max() / np.abs(ref).max()),
+            "max_abs_diff": float(np.abs(d).max()), "max_abs_ref": float(np.abs(ref).max())}
 
 
 def energy_block(r64, r32, work, t64_ms, t32_ms, rff=None, tff_ms=None):
@@ -403,7 +425,7 @@ def run_ours(args, world, rank, dev, pg):
     U0 = np.ascontiguousarray(initial_condition(X))
     chosen = set(args.variants.split(","))
     skipped = {"total_ms": float("nan"), "stage_ms": float("nan"), "ndof": None, "clocks": None, "epb": None,
-               "kernel": None, "l2_norm": None, "mass": None, "state_bytes": 0}
+               "kernel": None, "l2_norm": None, "mass": None, "state_bytes": 0, "final": None}
     log("initial condition ready")
     r64 = run_solver_timed("f64", args, dev, pg, U0) if "f64" in chosen else dict(skipped)
     log("f64 timed")
@@ -464,6 +486,13 @@ def run_ours(args, world, rank, dev, pg):
         "energy": energy_block(r64, r32, work, t64, t32, rff, tff),
         "check": {"l2_norm_f64": r64["l2_norm"], "l2_norm_f32": r32["l2_norm"], "l2_norm_f64_ff": rff["l2_norm"],
                   "mass_f64": r64["mass"]},
+        # the FP64 path matches the oracle to 1e-12 per step (tests), so these are the other
+        # precisions' errors against the method in FP64 after NSTEPS steps
+        "accuracy": {"steps": NSTEPS,
+                     "f32_vs_f64": (rel_err(r32["final"], r64["final"])
+                                    if r32.get("final") is not None and r64.get("final") is not None else None),
+                     "f64_ff_vs_f64": (rel_err(rff["final"], r64["final"])
+                                       if rff.get("final") is not None and r64.get("final") is not None else None)},
     }
     if rank == 0 and not args.no_cpu_baseline:
         rate, el = oracle_sample(args.cpu_steps)
