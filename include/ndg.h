@@ -63,6 +63,13 @@ enum { NDG_LAYOUT_ELEMENT = 0, NDG_LAYOUT_GRID = 1 };
  * shared memory (higher occupancy for isothermal Euler).
  * AUTO = the autotuned choice for the kernel class, else LINE. */
 enum { NDG_KERNEL_AUTO = 0, NDG_KERNEL_LINE = 1, NDG_KERNEL_LINE_VAR = 2 };
+/* Mass matrix of the element basis.  LUMPED (default): the paper's, int h_k h_l ~= w_k delta_kl by
+ * the LGL quadrature (Sec. 2.1, Eq. (lag_coefs)), so a face term lifts onto the end node only.
+ * EXACT: the exactly integrated mass matrix of the textbook nodal DG method the paper cites; the
+ * volume term is unchanged (the LGL quadrature of h_l times a degree N-1 polynomial is exact) and a
+ * face term lifts onto every node of the line by M^-1 e_0 / M^-1 e_N.  A correctness variant,
+ * not a faster one (two more multiply-adds per node and axis). */
+enum { NDG_MASS_LUMPED = 0, NDG_MASS_EXACT = 1 };
 
 typedef struct ndg_ctx ndg_ctx;     /* one solve: state, buffers, stream, launch plan */
 typedef struct ndg_batch ndg_batch; /* several solves stepped by one graph per RK step */
@@ -83,6 +90,7 @@ typedef struct {
   int elems_per_block;/* elements per CTA of the stage kernel; 0: library default */
   int device;         /* CUDA device ordinal; default 0 */
   int kernel;         /* NDG_KERNEL_AUTO (default), NDG_KERNEL_LINE or NDG_KERNEL_LINE_VAR */
+  int mass;           /* NDG_MASS_LUMPED (default) or NDG_MASS_EXACT */
 } ndg_config;
 
 /* Norms by LGL quadrature on every element (Sec. 3.1's L2 norm). */
@@ -108,7 +116,8 @@ typedef struct {
 } ndg_info_t;
 
 /* Fill cfg with defaults: 2D, degree 7, 16x16 elements, advection, upwind, FP64, unit square,
- * velocity (1,0,0), c = 1, stream NULL, elems_per_block 0, device 0.  Returns NDG_EINVAL on NULL. */
+ * velocity (1,0,0), c = 1, stream NULL, elems_per_block 0, device 0, lumped mass.  Returns
+ * NDG_EINVAL on NULL. */
 int ndg_config_init(ndg_config* cfg);
 
 /* Create a context (Sec. 2: NDG discretisation of a periodic box).  Builds the LGL basis on the

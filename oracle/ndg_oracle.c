@@ -29,7 +29,10 @@
  *   - L2 norm (Sec. 3.1) by LGL quadrature on every element.
  *
  * Readings of passages that are ambiguous or garbled in the paper:
- *   1. Mass matrix: lumped, int h_k h_l ~= w_k delta_kl (Eq. (lag_coefs)).
+ *   1. Mass matrix: lumped, int h_k h_l ~= w_k delta_kl (Eq. (lag_coefs)), as the paper's equations
+ *      state.  Its cited textbook NDG uses the exact mass matrix instead; that variant is kept as
+ *      an option (mass = ORC_MASS_EXACT): M[k][l] = int h_k h_l exactly (Gauss-Legendre
+ *      quadrature with N+1 points), and the weak form is solved with M in place of diag(w).
  *   2. Element map Eq. (transformation) has no element offset; x = x_{j-1/2} + (dx/2)(xi + 1).
  *   3. "N" is both the element count and the degree; here N is the degree, n = N+1 nodes/axis.
  *   4. Local Lax-Friedrichs: alpha = max over both sides of |lambda_max|; isothermal Euler has
@@ -55,6 +58,7 @@
 
 enum { ORC_ADVECTION = 0, ORC_ISO_EULER = 1 };
 enum { ORC_FLUX_UPWIND = 0, ORC_FLUX_LLF = 1 };
+enum { ORC_MASS_LUMPED = 0, ORC_MASS_EXACT = 1 };
 
 typedef struct {
   int dim;        /* 1, 2 or 3 */
@@ -65,6 +69,7 @@ typedef struct {
   double length[3]; /* domain [0, length[a]] per axis */
   double velocity[3]; /* advection velocity a */
   double sound_speed; /* isothermal sound speed (the paper's a in Eq. (eulerIso2d)) */
+  int mass;       /* ORC_MASS_LUMPED (the paper's) or ORC_MASS_EXACT */
 } orc_problem;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -139,6 +144,79 @@ int orc_dmat(int N, const double* xi, double* D) {
   return 0;
 }
 
+/* The Lagrange polynomial h_i of Eq. (lagrange_pol) on the nodes xi, evaluated at x. */
+static double lagrange(int N, const double* xi, int i, double x) {
+  double v = 1.0;
+  for (int j = 0; j <= N; ++j)
+    if (j != i) v *= (x - xi[j]) / (xi[i] - xi[j]);
+  return v;
+}
+
+/* Mass matrix of the Lagrange basis on the LGL nodes, M[k*(N+1) + l] ~ int_{-1}^{1} h_k h_l:
+ * exact = 0: lumped by the LGL quadrature of Eq. (lag_coefs), diag(w);
+ * exact = 1: integrated exactly by Gauss-Legendre quadrature with N+1 points (exact to degree
+ *            2N+1; the integrand has degree 2N).  Gauss nodes: Newton on P_{N+1} from the
+ *            usual cosine guesses; weights 2 / ((1 - x^2) P_{N+1}'(x)^2). */
+int orc_mass(int N, int exact, double* M) {
+  if (N < 1 || N >= ORC_MAXN) return -1;
+  int n = N + 1;
+  double xi[ORC_MAXN], w[ORC_MAXN];
+  orc_lgl(N, xi, w);
+  for (int q = 0; q < n * n; ++q) M[q] = 0.0;
+  if (!exact) {
+    for (int k = 0; k < n; ++k) M[k * n + k] = w[k];
+    return 0;
+  }
+  const double pi = 3.14159265358979323846;
+  const int m = n; /* Gauss points */
+  for (int q = 0; q < m; ++q) {
+    double x = cos(pi * (q + 0.75) / (m + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double pm, pm1;
+      legendre(m, x, &pm, &pm1);
+      dp = m * (x * pm - pm1) / (x * x - 1.0); /* P_m'(x) */
+      double step = pm / dp;
+      x -= step;
+      if (fabs(step) < 1e-16) break;
+    }
+    double pm, pm1;
+    legendre(m, x, &pm, &pm1);
+    dp = m * (x * pm - pm1) / (x * x - 1.0);
+    double wq = 2.0 / ((1.0 - x * x) * dp * dp);
+    double hv[ORC_MAXN];
+    for (int k = 0; k < n; ++k) hv[k] = lagrange(N, xi, k, x);
+    for (int k = 0; k < n; ++k)
+      for (int l = 0; l < n; ++l) M[k * n + l] += wq * hv[k] * hv[l];
+  }
+  return 0;
+}
+
+/* In-place inverse of the n x n matrix A (Gauss-Jordan elimination with partial pivoting). */
+static int invert(int n, double* A) {
+  double B[ORC_MAXN * ORC_MAXN];
+  for (int i = 0; i < n * n; ++i) B[i] = 0.0;
+  for (int i = 0; i < n; ++i) B[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return -1;
+    for (int j = 0; j < n; ++j) {
+      double t = A[c * n + j]; A[c * n + j] = A[piv * n + j]; A[piv * n + j] = t;
+      t = B[c * n + j]; B[c * n + j] = B[piv * n + j]; B[piv * n + j] = t;
+    }
+    double d = A[c * n + c];
+    for (int j = 0; j < n; ++j) { A[c * n + j] /= d; B[c * n + j] /= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = A[r * n + c];
+      for (int j = 0; j < n; ++j) { A[r * n + j] -= f * A[c * n + j]; B[r * n + j] -= f * B[c * n + j]; }
+    }
+  }
+  for (int i = 0; i < n * n; ++i) A[i] = B[i];
+  return 0;
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Problem geometry                                                                              */
 /* ------------------------------------------------------------------------------------------ */
@@ -168,6 +246,7 @@ static int check_problem(const orc_problem* p) {
     if (p->elems[a] < 1 || !(p->length[a] > 0.0)) return -1;
   if (p->equation != ORC_ADVECTION && p->equation != ORC_ISO_EULER) return -1;
   if (p->equation == ORC_ISO_EULER && p->flux != ORC_FLUX_LLF) return -1;
+  if (p->mass != ORC_MASS_LUMPED && p->mass != ORC_MASS_EXACT) return -1;
   return 0;
 }
 
@@ -248,6 +327,12 @@ int orc_rhs(const orc_problem* p, const double* U, double* R) {
   double xi[ORC_MAXN], w[ORC_MAXN], D[ORC_MAXN * ORC_MAXN];
   orc_lgl(N, xi, w);
   orc_dmat(N, xi, D);
+  const int exact = p->mass == ORC_MASS_EXACT;
+  double Minv[ORC_MAXN * ORC_MAXN];
+  if (exact) {
+    orc_mass(N, 1, Minv);
+    if (invert(n, Minv)) return -1;
+  }
   int E[3] = {1, 1, 1};
   for (int a = 0; a < d; ++a) E[a] = p->elems[a];
   int np = ipow(n, d);
@@ -256,7 +341,7 @@ int orc_rhs(const orc_problem* p, const double* U, double* R) {
   int stride[3] = {1, n, n * n}; /* node-index stride along each axis */
   for (int64_t q = 0; q < nd; ++q) R[q] = 0.0;
 
-  double u[ORC_MAXN][4], F[ORC_MAXN][4], uLn[4], uRn[4], fhatL[4], fhatR[4];
+  double u[ORC_MAXN][4], F[ORC_MAXN][4], uLn[4], uRn[4], fhatL[4], fhatR[4], b[ORC_MAXN][4];
   for (int64_t e = 0; e < ne; ++e) {
     int ei[3] = {(int)(e % E[0]), (int)((e / E[0]) % E[1]), (int)(e / ((int64_t)E[0] * E[1]))};
     for (int a = 0; a < d; ++a) {
@@ -288,7 +373,20 @@ int orc_rhs(const orc_problem* p, const double* U, double* R) {
             double surf = 0.0;
             if (l == N) surf -= fhatR[v];
             if (l == 0) surf += fhatL[v];
-            R[((int64_t)v * ne + e) * np + base + l * stride[a]] += (2.0 / h) * (vol + surf) / w[l];
+            b[l][v] = vol + surf;
+          }
+        }
+        /* solve with the mass matrix: lumped diag(w), or the exact M (reading 1) */
+        for (int l = 0; l < n; ++l) {
+          for (int v = 0; v < nv; ++v) {
+            double* out = &R[((int64_t)v * ne + e) * np + base + l * stride[a]];
+            if (!exact) {
+              *out += (2.0 / h) * b[l][v] / w[l];
+            } else {
+              double r = 0.0;
+              for (int m = 0; m < n; ++m) r += Minv[l * n + m] * b[m][v];
+              *out += (2.0 / h) * r;
+            }
           }
         }
       }

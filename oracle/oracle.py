@@ -25,6 +25,7 @@ _lib = None
 
 ADVECTION, ISO_EULER = 0, 1
 FLUX_UPWIND, FLUX_LLF = 0, 1
+MASS_LUMPED, MASS_EXACT = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -49,6 +50,7 @@ class _Problem(ctypes.Structure):
         ("length", ctypes.c_double * 3),
         ("velocity", ctypes.c_double * 3),
         ("sound_speed", ctypes.c_double),
+        ("mass", ctypes.c_int),
     ]
 
 
@@ -64,6 +66,7 @@ class Problem:
     length: tuple = (1.0, 1.0, 1.0)
     velocity: tuple = (1.0, 0.0, 0.0)
     sound_speed: float = 1.0
+    mass: int = MASS_LUMPED  # the paper's lumped mass, or the exact mass matrix (reading 1)
 
     @property
     def nvar(self) -> int:
@@ -94,7 +97,8 @@ class Problem:
         L = list(self.length) + [1.0] * (3 - len(self.length))
         a = list(self.velocity) + [0.0] * (3 - len(self.velocity))
         return _Problem(self.dim, self.degree, (ctypes.c_int * 3)(*e[:3]), self.equation, self.flux,
-                        (ctypes.c_double * 3)(*L[:3]), (ctypes.c_double * 3)(*a[:3]), self.sound_speed)
+                        (ctypes.c_double * 3)(*L[:3]), (ctypes.c_double * 3)(*a[:3]), self.sound_speed,
+                        self.mass)
 
 
 def _load():
@@ -106,6 +110,7 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             lib.orc_lgl.argtypes = [ctypes.c_int, dp, dp]
             lib.orc_dmat.argtypes = [ctypes.c_int, dp, dp]
+            lib.orc_mass.argtypes = [ctypes.c_int, ctypes.c_int, dp]
             lib.orc_rhs.argtypes = [P, dp, dp]
             lib.orc_step.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
             lib.orc_norms.argtypes = [P, dp, dp, dp]
@@ -143,6 +148,14 @@ def dmat(N: int) -> np.ndarray:
     D = np.zeros((N + 1) * (N + 1))
     _load().orc_dmat(N, _ptr(xi), _ptr(D))
     return D.reshape(N + 1, N + 1)
+
+
+def mass(N: int, exact: bool = True) -> np.ndarray:
+    """Mass matrix of the Lagrange basis on the LGL nodes: exact (Gauss quadrature) or lumped."""
+    M = np.zeros((N + 1) * (N + 1))
+    if _load().orc_mass(N, int(bool(exact)), _ptr(M)) != 0:
+        raise ValueError("bad degree")
+    return M.reshape(N + 1, N + 1)
 
 
 def node_coords(p: Problem) -> np.ndarray:

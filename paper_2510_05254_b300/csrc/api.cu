@@ -38,13 +38,24 @@ NDG_DECL(stage_f32_d3)
 NDG_DECL(stage_f64ff_d1)
 NDG_DECL(stage_f64ff_d2)
 NDG_DECL(stage_f64ff_d3)
+NDG_DECL(stage_f64x_d1)
+NDG_DECL(stage_f64x_d2)
+NDG_DECL(stage_f64x_d3)
+NDG_DECL(stage_f32x_d1)
+NDG_DECL(stage_f32x_d2)
+NDG_DECL(stage_f32x_d3)
 #undef NDG_DECL
 
 namespace {
+// Tables by [dtype][dim - 1]; the exact-mass classes (FP64 and FP32 only) by [dtype][dim - 1]
+// of the second table.
 LaunchFn pick_launch(const KernelClass& k) {
   static LaunchFn (*t[3][3])(int, int) = {{stage_f64_d1_launch, stage_f64_d2_launch, stage_f64_d3_launch},
                                           {stage_f32_d1_launch, stage_f32_d2_launch, stage_f32_d3_launch},
                                           {stage_f64ff_d1_launch, stage_f64ff_d2_launch, stage_f64ff_d3_launch}};
+  static LaunchFn (*x[2][3])(int, int) = {{stage_f64x_d1_launch, stage_f64x_d2_launch, stage_f64x_d3_launch},
+                                          {stage_f32x_d1_launch, stage_f32x_d2_launch, stage_f32x_d3_launch}};
+  if (k.mass == NDG_MASS_EXACT) return k.dtype < 2 ? x[k.dtype][k.dim - 1](k.degree, k.equation) : nullptr;
   return t[k.dtype][k.dim - 1](k.degree, k.equation);
 }
 PrepareFn pick_prepare(const KernelClass& k) {
@@ -52,12 +63,17 @@ PrepareFn pick_prepare(const KernelClass& k) {
       {stage_f64_d1_prepare, stage_f64_d2_prepare, stage_f64_d3_prepare},
       {stage_f32_d1_prepare, stage_f32_d2_prepare, stage_f32_d3_prepare},
       {stage_f64ff_d1_prepare, stage_f64ff_d2_prepare, stage_f64ff_d3_prepare}};
+  static PrepareFn (*x[2][3])(int, int) = {
+      {stage_f64x_d1_prepare, stage_f64x_d2_prepare, stage_f64x_d3_prepare},
+      {stage_f32x_d1_prepare, stage_f32x_d2_prepare, stage_f32x_d3_prepare}};
+  if (k.mass == NDG_MASS_EXACT) return k.dtype < 2 ? x[k.dtype][k.dim - 1](k.degree, k.equation) : nullptr;
   return t[k.dtype][k.dim - 1](k.degree, k.equation);
 }
 ShapeFn pick_shape(const KernelClass& k) {
   static ShapeFn (*t[3][3])(int, int) = {{stage_f64_d1_shape, stage_f64_d2_shape, stage_f64_d3_shape},
                                          {stage_f32_d1_shape, stage_f32_d2_shape, stage_f32_d3_shape},
                                          {stage_f64ff_d1_shape, stage_f64ff_d2_shape, stage_f64ff_d3_shape}};
+  // the exact-mass kernels have the lumped ones' shapes
   return t[k.dtype][k.dim - 1](k.degree, k.equation);
 }
 }  // namespace
@@ -328,10 +344,11 @@ TileConfig default_tile(const KernelClass& kc) {
 std::mutex g_tune_mu;
 std::map<long long, TileConfig> g_tuned;
 long long class_key(const KernelClass& k) {
-  return (((long long)k.dim * 16 + k.degree) * 2 + k.equation) * 4 + k.dtype;
+  return ((((long long)k.dim * 16 + k.degree) * 2 + k.equation) * 4 + k.dtype) * 2 + k.mass;
 }
 // Optional persistent cache: NDG_AUTOTUNE_CACHE names a text file of lines
-// "dim degree equation dtype epb variant", read once per process, rewritten after each autotune.
+// "dim degree equation dtype mass epb variant", read once per process, rewritten after each
+// autotune (lines of another form are skipped).
 bool g_tune_loaded = false;
 void load_tune_cache_locked() {
   if (g_tune_loaded) return;
@@ -340,10 +357,13 @@ void load_tune_cache_locked() {
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int d, n, e, t, epb, var;
-  while (std::fscanf(f, "%d %d %d %d %d %d", &d, &n, &e, &t, &epb, &var) == 6)
-    if (epb > 0 && epb <= 1024 && (var == kLineKernel || var == kLineVarKernel))
-      g_tuned.emplace(class_key(KernelClass{d, n, e, t}), TileConfig{epb, var});
+  char line[256];
+  while (std::fgets(line, sizeof(line), f)) {
+    int d, n, e, t, m, epb, var;
+    if (std::sscanf(line, "%d %d %d %d %d %d %d", &d, &n, &e, &t, &m, &epb, &var) != 7) continue;
+    if (epb > 0 && epb <= 1024 && (var == kLineKernel || var == kLineVarKernel) && (m == 0 || m == 1))
+      g_tuned.emplace(class_key(KernelClass{d, n, e, t, m}), TileConfig{epb, var});
+  }
   std::fclose(f);
 }
 void save_tune_cache_locked() {
@@ -354,8 +374,10 @@ void save_tune_cache_locked() {
   if (!f) return;
   for (auto& kv : g_tuned) {
     long long key = kv.first;
+    const int mass = (int)(key % 2);
+    key /= 2;
     const int dtype = (int)(key % 4), eq = (int)((key / 4) % 2), deg = (int)((key / 8) % 16), dim = (int)(key / 128);
-    std::fprintf(f, "%d %d %d %d %d %d\n", dim, deg, eq, dtype, kv.second.epb, kv.second.variant);
+    std::fprintf(f, "%d %d %d %d %d %d %d\n", dim, deg, eq, dtype, mass, kv.second.epb, kv.second.variant);
   }
   std::fclose(f);
   std::rename(tmp.c_str(), path);
@@ -558,6 +580,9 @@ int check_config(const ndg_config& k) {
   if (k.elems_per_block < 0) return fail(NDG_EINVAL, "elems_per_block must be >= 0");
   if (k.kernel != NDG_KERNEL_AUTO && k.kernel != NDG_KERNEL_LINE && k.kernel != NDG_KERNEL_LINE_VAR)
     return fail(NDG_EINVAL, "unknown kernel mapping %d", k.kernel);
+  if (k.mass != NDG_MASS_LUMPED && k.mass != NDG_MASS_EXACT) return fail(NDG_EINVAL, "unknown mass matrix %d", k.mass);
+  if (k.mass == NDG_MASS_EXACT && k.dtype == NDG_F64_FF)
+    return fail(NDG_EINVAL, "the exact mass matrix is built for NDG_F64 and NDG_F32");
   return NDG_OK;
 }
 
@@ -637,7 +662,7 @@ int ndg_create_ex(const ndg_config* cfg, ndg_ctx** out) {
     c->cfg.elems[a] = 1;
     c->cfg.velocity[a] = 0.0;
   }
-  c->kc = KernelClass{k.dim, k.degree, k.equation, k.dtype};
+  c->kc = KernelClass{k.dim, k.degree, k.equation, k.dtype, k.mass};
   c->n = k.degree + 1;
   c->npe = 1;
   for (int a = 0; a < k.dim; ++a) c->npe *= c->n;

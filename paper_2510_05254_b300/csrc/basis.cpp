@@ -120,6 +120,16 @@ bool build_basis(int N, Basis* b) {
   long double V[kMaxN * kMaxN], Vr[kMaxN * kMaxN];
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) legendre_on(j, x[i], &V[i * n + j], &Vr[i * n + j]);
+  // M^-1 = V V^T (orthonormal modal basis): the exact-mass lift vectors, scaled by the end weights
+  for (int l = 0; l < n; ++l) {
+    long double lo = 0.0L, hi = 0.0L;
+    for (int j = 0; j < n; ++j) {
+      lo += V[l * n + j] * V[0 * n + j];
+      hi += V[l * n + j] * V[N * n + j];
+    }
+    b->lift_exact_lo[l] = (double)(lo * b->w[0]);
+    b->lift_exact_hi[l] = (double)(hi * b->w[N]);
+  }
   if (!invert(n, V)) return false;
   long double D[kMaxN * kMaxN];
   for (int i = 0; i < n; ++i)

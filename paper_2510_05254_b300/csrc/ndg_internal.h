@@ -20,6 +20,10 @@ struct Basis {
   double Bo[kMaxN * kMaxN];
   double Cmid[kMaxN];        // D[i][mid] for odd n
   double Dmid[kMaxN];        // D[mid][m] for odd n
+  // exact mass matrix M (= (V V^T)^-1 for the orthonormal Legendre Vandermonde V): the lift
+  // vectors w_0 M^-1 e_0 and w_N M^-1 e_N (the lumped mass gives the unit vectors e_0, e_N)
+  double lift_exact_lo[kMaxN];
+  double lift_exact_hi[kMaxN];
 };
 
 bool build_basis(int N, Basis* b);
@@ -92,8 +96,9 @@ inline int dtype_bytes(int dtype) { return dtype == 1 ? 4 : 8; }
 // Kernel class: everything that is a template parameter of the stage kernel.
 struct KernelClass {
   int dim, degree, equation, dtype;
+  int mass = 0;  // NDG_MASS_LUMPED / NDG_MASS_EXACT (separate kernel instantiations)
   bool operator==(const KernelClass& o) const {
-    return dim == o.dim && degree == o.degree && equation == o.equation && dtype == o.dtype;
+    return dim == o.dim && degree == o.degree && equation == o.equation && dtype == o.dtype && mass == o.mass;
   }
 };
 

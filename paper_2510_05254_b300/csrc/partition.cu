@@ -234,7 +234,7 @@ int ndg_partition_create(const ndg_config* gcfg, const int parts[3], ndg_partiti
   // the partitions' descriptors as one group, with halo buffers on every partition boundary
   ndg_info_t info;
   ndg_info(P->ctx[0], &info);
-  P->group.kc = KernelClass{gcfg->dim, gcfg->degree, gcfg->equation, gcfg->dtype};
+  P->group.kc = KernelClass{gcfg->dim, gcfg->degree, gcfg->equation, gcfg->dtype, gcfg->mass};
   P->group.epb = info.elems_per_block;
   P->group.variant = info.kernel == NDG_KERNEL_LINE_VAR ? kLineVarKernel : kLineKernel;
   int L = 1;

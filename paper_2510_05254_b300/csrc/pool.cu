@@ -4,7 +4,7 @@
 //   - callers: ndg_pool_submit copies the initial state into host memory and queues the solve;
 //   - the worker: admits queued solves first-in first-out while the budget allows, and steps
 //     every running solve together, one CUDA-graph replay per RK step.  Solves of one kernel
-//     class (dim, degree, equation, dtype, RK scheme) share one persistent stage launch per
+//     class (dim, degree, equation, dtype, mass matrix, RK scheme) share one persistent stage launch per
 //     stage; classes are parallel branches of the graph.  The graph reads its work lists from
 //     device memory, so solves join and leave at step boundaries by rewriting those lists; it
 //     is captured again only when a class first appears or a list outgrows its capacity;
@@ -61,7 +61,7 @@ struct PoolSolve {
 };
 
 long long pool_class_key(const KernelClass& k, int rk) {
-  return ((((long long)k.dim * 16 + k.degree) * 2 + k.equation) * 4 + k.dtype) * 8 + rk;
+  return (((((long long)k.dim * 16 + k.degree) * 2 + k.equation) * 4 + k.dtype) * 2 + k.mass) * 8 + rk;
 }
 
 struct PoolClass {
@@ -413,7 +413,7 @@ int ndg_pool_submit(ndg_pool* p, const ndg_config* cfg, const void* u0, size_t n
     s->cfg.elems[a] = 1;
     s->cfg.velocity[a] = 0.0;
   }
-  s->kc = KernelClass{cfg->dim, cfg->degree, cfg->equation, cfg->dtype};
+  s->kc = KernelClass{cfg->dim, cfg->degree, cfg->equation, cfg->dtype, cfg->mass};
   s->rk = rk;
   s->dt = dt;
   s->nsteps = nsteps;

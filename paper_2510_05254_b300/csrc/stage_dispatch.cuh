@@ -1,5 +1,6 @@
 // Instantiation of the fused stage kernel for one (precision, dimension) pair, degrees 1..7 and
-// both equations.  Each stage_<dtype>_d<dim>.cu includes this with NDG_REAL / NDG_DIM defined.
+// both equations.  Each stage_<dtype>_d<dim>.cu includes this with NDG_REAL / NDG_DIM defined
+// (and NDG_FF / NDG_EXACT for the float-float and exact-mass variants).
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -12,6 +13,9 @@ namespace {
 
 #ifndef NDG_FF
 #define NDG_FF false
+#endif
+#ifndef NDG_EXACT
+#define NDG_EXACT false  // exact-mass variant (NDG_MASS_EXACT)
 #endif
 
 const BasisFF& basis_ff(int N) {
@@ -62,6 +66,10 @@ const BasisArgs<real>& basis_args(int N) {
         t.Cmid[i] = (real)b.Cmid[i];
         t.Dmid[i] = (real)b.Dmid[i];
       }
+      for (int l = 0; l < n; ++l) {
+        t.Llo[l] = (real)b.lift_exact_lo[l];
+        t.Lhi[l] = (real)b.lift_exact_hi[l];
+      }
     }
   });
   return table[N];
@@ -77,7 +85,7 @@ void shape_of(int variant, int epb, int* threads, size_t* smem) {
 
 template <int N, int EQ, bool VS>
 void launch_kernel(int grid, int threads, size_t smem, void* stream, const StageArgs<NDG_REAL>& args) {
-  stage_entry<NDG_DIM, N, EQ, NDG_REAL, VS, NDG_FF>()<<<grid, threads, smem, (cudaStream_t)stream>>>(args);
+  stage_entry<NDG_DIM, N, EQ, NDG_REAL, VS, NDG_FF, NDG_EXACT>()<<<grid, threads, smem, (cudaStream_t)stream>>>(args);
 }
 
 template <int N, int EQ>
@@ -100,8 +108,8 @@ int launch_one(int variant, int grid, int epb, const SolveDesc* solves, const Gr
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaFuncAttributes fa{};
-    if (variant == kLineVarKernel) cudaFuncGetAttributes(&fa, stage_entry<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF>());
-    else cudaFuncGetAttributes(&fa, stage_entry<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF>());
+    if (variant == kLineVarKernel) cudaFuncGetAttributes(&fa, stage_entry<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF, NDG_EXACT>());
+    else cudaFuncGetAttributes(&fa, stage_entry<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF, NDG_EXACT>());
     launch_error_detail(grid, threads, smem, fa.maxThreadsPerBlock, fa.numRegs, fa.localSizeBytes,
                         fa.maxDynamicSharedSizeBytes);
   }
@@ -129,8 +137,8 @@ int prepare_one(int variant, int epb, int* max_blocks) {
   shape_of<N, EQ>(variant, epb, &threads, &smem);
   if (threads > 1024 || threads < 1) return (int)cudaErrorInvalidConfiguration;
   if (variant == kLineVarKernel)
-    return occupancy(stage_entry<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF>(), threads, smem, max_blocks);
-  return occupancy(stage_entry<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF>(), threads, smem, max_blocks);
+    return occupancy(stage_entry<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF, NDG_EXACT>(), threads, smem, max_blocks);
+  return occupancy(stage_entry<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF, NDG_EXACT>(), threads, smem, max_blocks);
 }
 
 template <int N, int EQ>

@@ -42,6 +42,8 @@ struct BasisArgs {
   real Bo[16];
   real Cmid[4];  // D[i][mid], odd n
   real Dmid[4];  // D[mid][m], odd n
+  real Llo[8];   // exact mass: w_0 (M^-1 e_0)_l, the lift of the low face term onto node l
+  real Lhi[8];   // exact mass: w_N (M^-1 e_N)_l
 };
 
 template <typename real>
@@ -415,7 +417,8 @@ struct StageGeom {
 // of the face flux are computed once per line).  VS = true: a thread owns one (line, variable)
 // pair, so an Euler CTA has nvar times more threads for the same shared memory; the operations
 // per variable are the same, in the same order, so the results are bitwise identical.
-template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
+// EXACT: the exact-mass variant (face terms lifted by M^-1 e_0 / M^-1 e_N onto every node).
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
@@ -625,11 +628,17 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
             load_line<n, G::XW>(sUe, pstride, VX, f);
             contract_line<N, real, FF>(f, out, args);
             if (last) operands(0, bb, aa);
+            const real flo = xlo - f[0], fhi = f[N] - xhi;
 #pragma unroll
             for (int l = 0; l < n; ++l) {
               real r = (a == 0) ? out[l] : fma(vs, out[l], sRe[l * pstride]);
-              if (l == 0 && has_lo) r = fma(qlo, xlo - f[0], r);
-              if (l == N && has_hi) r = fma(qhi, f[N] - xhi, r);
+              if constexpr (!EXACT) {
+                if (l == 0 && has_lo) r = fma(qlo, flo, r);
+                if (l == N && has_hi) r = fma(qhi, fhi, r);
+              } else {
+                if (has_lo) r = fma(qlo * args.basis.Llo[l], flo, r);
+                if (has_hi) r = fma(qhi * args.basis.Lhi[l], fhi, r);
+              }
               if (last) stage_update_node(args, S, si, plan, gline + l * ustride, r, bb[l], aa[l]);
               else rr[l] = r;
             }
@@ -732,13 +741,20 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
             real* sRv = sRe + v * epb * SPE;
             if (last) operands(v, bb, aa);
             const long long gv = v * vstride + gline;
+            // (Fhat_lo - F(U_0)) = 1/2 (F(ext) - F(U_0) - alpha (U_0 - ext)); qlo carries the 1/2
+            const real flo = fma(-alo, u0 - xlo[v], fxlo - f[0]);
+            // (F(U_N) - Fhat_hi) = 1/2 (F(U_N) - F(ext) + alpha (ext - U_N))
+            const real fhi = fma(ahi, xhi[v] - uN, f[N] - fxhi);
 #pragma unroll
             for (int l = 0; l < n; ++l) {
               real r = (a == 0) ? out[l] : fma(vs, out[l], sRv[l * pstride]);
-              // (Fhat_lo - F(U_0)) = 1/2 (F(ext) - F(U_0) - alpha (U_0 - ext)); qlo carries the 1/2
-              if (l == 0) r = fma(qlo, fma(-alo, u0 - xlo[v], fxlo - f[0]), r);
-              // (F(U_N) - Fhat_hi) = 1/2 (F(U_N) - F(ext) + alpha (ext - U_N))
-              if (l == N) r = fma(qhi, fma(ahi, xhi[v] - uN, f[N] - fxhi), r);
+              if constexpr (!EXACT) {
+                if (l == 0) r = fma(qlo, flo, r);
+                if (l == N) r = fma(qhi, fhi, r);
+              } else {
+                r = fma(qlo * args.basis.Llo[l], flo, r);
+                r = fma(qhi * args.basis.Lhi[l], fhi, r);
+              }
               if (last) stage_update_node(args, S, si, plan, gv + l * ustride, r, bb[l], aa[l]);
               else rr[l] = r;
             }
@@ -801,22 +817,22 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   }
 }
 
-template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 __global__ void stage_kernel(const StageArgs<real> args) {
-  stage_body<DIM, N, EQ, real, VS, FF>(args);
+  stage_body<DIM, N, EQ, real, VS, FF, EXACT>(args);
 }
 // The same with the register budget capped at 96 per thread (no spills), used for FP32 3D: one CTA
 // per SM more than the compiler's own choice of 106 allows (FP32 3D Euler 1.34 -> 1.24 ms per
 // stage).  A cap on the other classes would not be neutral: it changes the compiler's allocation.
-template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 __global__ void __maxnreg__(96) stage_kernel_r96(const StageArgs<real> args) {
-  stage_body<DIM, N, EQ, real, VS, FF>(args);
+  stage_body<DIM, N, EQ, real, VS, FF, EXACT>(args);
 }
 // The entry point of a kernel class.
-template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false>
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 constexpr auto stage_entry() {
-  if constexpr (DIM == 3 && sizeof(real) == 4) return &stage_kernel_r96<DIM, N, EQ, real, VS, FF>;
-  else return &stage_kernel<DIM, N, EQ, real, VS, FF>;
+  if constexpr (DIM == 3 && sizeof(real) == 4) return &stage_kernel_r96<DIM, N, EQ, real, VS, FF, EXACT>;
+  else return &stage_kernel<DIM, N, EQ, real, VS, FF, EXACT>;
 }
 
 template <int DIM, int N, int EQ, typename real, bool VS>

@@ -21,6 +21,7 @@ NDG_RK3, NDG_RK4, NDG_RK6 = 3, 4, 6
 NDG_F64, NDG_F32, NDG_F64_FF = 0, 1, 2
 NDG_LAYOUT_ELEMENT, NDG_LAYOUT_GRID = 0, 1
 NDG_KERNEL_AUTO, NDG_KERNEL_LINE, NDG_KERNEL_LINE_VAR = 0, 1, 2
+NDG_MASS_LUMPED, NDG_MASS_EXACT = 0, 1
 STATUS_NAMES = {0: "NDG_OK", 1: "NDG_EINVAL", 2: "NDG_ENOMEM", 3: "NDG_ECUDA", 4: "NDG_ENONFINITE",
                 5: "NDG_EAGAIN", 6: "NDG_ETIMEOUT", 7: "NDG_ESTATE"}
 
@@ -36,7 +37,8 @@ class ndg_config(ctypes.Structure):
                 ("equation", ctypes.c_int), ("flux", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("length", ctypes.c_double * 3), ("velocity", ctypes.c_double * 3),
                 ("sound_speed", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("elems_per_block", ctypes.c_int), ("device", ctypes.c_int), ("kernel", ctypes.c_int)]
+                ("elems_per_block", ctypes.c_int), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("mass", ctypes.c_int)]
 
 
 class ndg_norms_t(ctypes.Structure):

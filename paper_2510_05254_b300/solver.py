@@ -20,7 +20,8 @@ class Solver:
     def __init__(self, dim: int, degree: int, elems, equation: int = nat.NDG_ADVECTION,
                  flux: int | None = None, dtype: str = "f64", length=(1.0, 1.0, 1.0),
                  velocity=(1.0, 0.0, 0.0), sound_speed: float = 1.0, elems_per_block: int = 0,
-                 device: int = 0, stream: torch.cuda.Stream | None = None, kernel: int = 0):
+                 device: int = 0, stream: torch.cuda.Stream | None = None, kernel: int = 0,
+                 mass: int = 0):
         if flux is None:
             flux = nat.NDG_FLUX_UPWIND if equation == nat.NDG_ADVECTION else nat.NDG_FLUX_LLF
         self.dtype_code, self.torch_dtype, self.np_dtype = DTYPES[dtype]
@@ -39,6 +40,7 @@ class Solver:
         cfg.elems_per_block = elems_per_block
         cfg.device = device
         cfg.kernel = kernel
+        cfg.mass = mass  # nat.NDG_MASS_LUMPED (the paper's) or nat.NDG_MASS_EXACT
         self.cfg = cfg
         self.dim, self.degree = dim, degree
         self.ctx = nat.ndg_create_ex(cfg)

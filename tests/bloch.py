@@ -35,8 +35,25 @@ def lgl_basis(N: int):
     return x, w, D
 
 
-def line_operator(N, A, alpha, h, theta):
-    """(n*nvar) x (n*nvar) operator of one 1D line, ordering [node][var]."""
+def lift_vectors(N, mass="lumped"):
+    """M^-1 e_0 and M^-1 e_N: the lift of a face term onto the line's nodes.  Lumped mass: the
+    end-node unit vectors over the LGL weights.  Exact mass: M^-1 = V V^T with V the orthonormal
+    Legendre Vandermonde at the nodes (M = (V V^T)^-1 for an orthonormal modal basis)."""
+    x, w, _ = lgl_basis(N)
+    n = N + 1
+    if mass == "lumped":
+        l0 = np.zeros(n); l0[0] = 1.0 / w[0]
+        lN = np.zeros(n); lN[N] = 1.0 / w[N]
+        return l0, lN
+    V = npleg.legvander(x, N) * np.sqrt((2.0 * np.arange(n) + 1.0) / 2.0)
+    Minv = V @ V.T
+    return Minv[:, 0], Minv[:, N]
+
+
+def line_operator(N, A, alpha, h, theta, mass="lumped"):
+    """(n*nvar) x (n*nvar) operator of one 1D line, ordering [node][var].  With the exact mass
+    matrix the strong form keeps -D F (W D F = M D F: the LGL quadrature of h_l times a degree
+    N-1 polynomial is exact) and lifts the face terms by M^-1 e_0, M^-1 e_N instead."""
     x, w, D = lgl_basis(N)
     n = N + 1
     A = np.atleast_2d(np.asarray(A, dtype=complex))
@@ -45,22 +62,23 @@ def line_operator(N, A, alpha, h, theta):
     L = -np.kron(D, A).astype(complex)
     eN = np.zeros(n); eN[N] = 1.0
     e0 = np.zeros(n); e0[0] = 1.0
+    l0, lN = lift_vectors(N, mass)
     ph = np.exp(1j * theta)
-    # right face: (F_N - Fhat_R)/w_N = 1/2 (A - alpha)(u_N - e^{i theta} u_0) / w_N
-    L += np.kron(np.outer(eN, eN - ph * e0), 0.5 * (A - alpha * I)) / w[N]
-    # left face: (Fhat_L - F_0)/w_0 = 1/2 (A + alpha)(e^{-i theta} u_N - u_0) / w_0
-    L += np.kron(np.outer(e0, np.conj(ph) * eN - e0), 0.5 * (A + alpha * I)) / w[0]
+    # right face: M^-1 e_N (F_N - Fhat_R) = M^-1 e_N 1/2 (A - alpha)(u_N - e^{i theta} u_0)
+    L += np.kron(np.outer(lN, eN - ph * e0), 0.5 * (A - alpha * I))
+    # left face: M^-1 e_0 (Fhat_L - F_0) = M^-1 e_0 1/2 (A + alpha)(e^{-i theta} u_N - u_0)
+    L += np.kron(np.outer(l0, np.conj(ph) * eN - e0), 0.5 * (A + alpha * I))
     return (2.0 / h) * L
 
 
-def element_operator(dim, N, As, alphas, hs, thetas):
+def element_operator(dim, N, As, alphas, hs, thetas, mass="lumped"):
     """Full element operator with ordering [var][node], node = i + n j + n^2 k (i fastest)."""
     n = N + 1
     nv = np.atleast_2d(As[0]).shape[0]
     npe = n ** dim
     total = np.zeros((nv * npe, nv * npe), dtype=complex)
     for a in range(dim):
-        La = line_operator(N, As[a], alphas[a], hs[a], thetas[a])  # [node_a][var] ordering
+        La = line_operator(N, As[a], alphas[a], hs[a], thetas[a], mass)  # [node_a][var] ordering
         La4 = La.reshape(n, nv, n, nv)  # (l, v, k, u)
         # embed: node multi-index (i0, i1, i2), axis a varies, others identity
         for base in range(npe):

@@ -476,3 +476,56 @@ def test_advection_with_zero_velocity_components(dim, N, E, vel, dtype):
         assert rel_l2(s.get_state(), orc.step(p, U.astype(np.float32).astype(np.float64), dt, 1, 4)) < F32_TOL
     else:
         check(p, s, U, dt, 2, 4, F64_TOL)
+
+
+# ---- the exact-mass variant (NDG_MASS_EXACT) against the oracle's exact-mass weak form ----
+
+@pytest.mark.parametrize("dim,N,E,eq", [(1, 4, (7,), 1), (1, 3, (6,), 0), (2, 7, (5, 3), 0), (2, 7, (4, 3), 1),
+                                        (2, 4, (5, 4), 1), (3, 2, (3, 2, 3), 1), (3, 5, (2, 3, 2), 1),
+                                        (3, 3, (2, 2, 3), 0)])
+def test_exact_mass_variant(dim, N, E, eq):
+    """FP64 within 1e-12 per step (RK4 and RK6, both thread mappings, ragged tiles) and FP32 within
+    its tolerance, on a state whose faces jump (the lift differs from the lumped one there)."""
+    flux = 0 if eq == 0 else 1
+    kw = dict(equation=eq, flux=flux, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3), mass=nat.NDG_MASS_EXACT)
+    p = orc.Problem(dim=dim, degree=N, elems=E + (1,) * (3 - len(E)), equation=eq, flux=flux,
+                    length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3), mass=orc.MASS_EXACT)
+    U = initial(p)
+    dt = 0.5 * orc.stable_dt(p, U, 0.2)
+    for kern in (nat.NDG_KERNEL_LINE, nat.NDG_KERNEL_LINE_VAR):
+        for rk in (4, 6):
+            s = Solver(dim, N, E, elems_per_block=2, kernel=kern, **kw)
+            check(p, s, U, dt, 2, rk, F64_TOL)
+    s = Solver(dim, N, E, elems_per_block=3, dtype="f32", **kw)
+    s.set_state(U)
+    s.step(dt, 2, 4)
+    ref = orc.step(p, U.astype(np.float32).astype(np.float64), dt, 2, 4)
+    assert rel_l2(s.get_state(), ref) < 2 * F32_TOL
+    # and it is a different scheme: the lumped solve moves away from it
+    s = Solver(dim, N, E, elems_per_block=2, **dict(kw, mass=nat.NDG_MASS_LUMPED))
+    s.set_state(U)
+    s.step(dt, 2, 4)
+    assert rel_l2(s.get_state(), orc.step(p, U, dt, 2, 4)) > 1e-9
+
+
+def test_exact_mass_rejected_for_float_float_and_batches_apart():
+    with pytest.raises(nat.NdgError) as ei:
+        Solver(2, 3, (4, 4), dtype="f64ff", mass=nat.NDG_MASS_EXACT)
+    assert ei.value.status == nat.NDG_EINVAL
+    # a batch of an exact-mass and a lumped solve of the same shape: each as alone
+    p = orc.Problem(dim=2, degree=5, elems=(4, 3, 1), equation=1, flux=1, mass=orc.MASS_EXACT)
+    U = initial(p)
+    dt = 0.5 * orc.stable_dt(p, U, 0.2)
+    outs = []
+    for m in (nat.NDG_MASS_EXACT, nat.NDG_MASS_LUMPED):
+        s = Solver(2, 5, (4, 3), equation=1, mass=m)
+        s.set_state(U)
+        s.step(dt, 3, 4)
+        outs.append(s.get_state())
+    a = Solver(2, 5, (4, 3), equation=1, mass=nat.NDG_MASS_EXACT)
+    b = Solver(2, 5, (4, 3), equation=1, mass=nat.NDG_MASS_LUMPED)
+    a.set_state(U)
+    b.set_state(U)
+    batch = Batch([a, b])
+    batch.step([dt, dt], 3, 4)
+    assert np.array_equal(a.get_state(), outs[0]) and np.array_equal(b.get_state(), outs[1])
