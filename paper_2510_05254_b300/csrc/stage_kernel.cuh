@@ -262,38 +262,44 @@ struct LineTrace {
   long long hoff, hvs;  // halo offset of this line's face node (variable 0), stride per variable
 };
 
+// Element coordinates of element index eu: two divisions, once per thread and tile, instead of
+// several per axis and line.
+struct ElemXYZ {
+  unsigned x, y, z;
+};
+__device__ __forceinline__ ElemXYZ elem_xyz(unsigned eu, unsigned E0, unsigned E1) {
+  const unsigned r = eu / E0;
+  return ElemXYZ{eu - r * E0, r % E1, r / E1};
+}
+
 template <int L>
-__device__ __forceinline__ LineTrace line_trace(int a, unsigned eu, int line, unsigned E0, unsigned E1,
-                                                unsigned E2, long long nelem, bool halo_lo, bool halo_hi) {
+__device__ __forceinline__ LineTrace line_trace(int a, unsigned eu, ElemXYZ c, int line, unsigned E0, unsigned E1,
+                                                unsigned E2, bool halo_lo, bool halo_hi) {
   LineTrace t;
-  unsigned lo_, hi_, te, ca, Ea;
+  unsigned lo_, hi_, te, ca, Ea, ntrans;
   if (a == 0) {
-    const unsigned ex = eu % E0;
-    ca = ex; Ea = E0; te = eu / E0;
-    lo_ = eu - ex + (ex == 0 ? E0 - 1 : ex - 1);
-    hi_ = eu - ex + (ex == E0 - 1 ? 0 : ex + 1);
+    ca = c.x; Ea = E0; te = c.y + E1 * c.z; ntrans = E1 * E2;
+    lo_ = c.x == 0 ? eu + (E0 - 1) : eu - 1;
+    hi_ = c.x == E0 - 1 ? eu - (E0 - 1) : eu + 1;
   } else if (a == 1) {
-    const unsigned ey = (eu / E0) % E1;
-    ca = ey; Ea = E1; te = eu % E0 + E0 * (eu / (E0 * E1));
-    lo_ = ey == 0 ? eu + (E1 - 1) * E0 : eu - E0;
-    hi_ = ey == E1 - 1 ? eu - (E1 - 1) * E0 : eu + E0;
+    ca = c.y; Ea = E1; te = c.x + E0 * c.z; ntrans = E0 * E2;
+    lo_ = c.y == 0 ? eu + (E1 - 1) * E0 : eu - E0;
+    hi_ = c.y == E1 - 1 ? eu - (E1 - 1) * E0 : eu + E0;
   } else {
     const unsigned step = E0 * E1;
-    const unsigned ez = eu / step;
-    ca = ez; Ea = E2; te = eu % step;
-    lo_ = ez == 0 ? eu + (E2 - 1) * step : eu - step;
-    hi_ = ez == E2 - 1 ? eu - (E2 - 1) * step : eu + step;
+    ca = c.z; Ea = E2; te = c.x + E0 * c.y; ntrans = step;
+    lo_ = c.z == 0 ? eu + (E2 - 1) * step : eu - step;
+    hi_ = c.z == E2 - 1 ? eu - (E2 - 1) * step : eu + step;
   }
   t.elo = lo_;
   t.ehi = hi_;
   t.lo_halo = ca == 0 && halo_lo;
   t.hi_halo = ca == Ea - 1 && halo_hi;
   t.hoff = (long long)te * L + line;
-  t.hvs = (long long)(nelem / Ea) * L;
+  t.hvs = (long long)ntrans * L;  // transverse elements x lines: one variable's halo
   return t;
 }
 
-// Padded shared-memory base / stride and unpadded node base / stride of line `line` along axis a.
 // (x-lines in shared memory start RS slots apart: RS = n + 1, or a multiple of 4 for 16-byte access)
 template <int n, int RS>
 __device__ __forceinline__ void line_geometry(int a, int line, int& pbase, int& pstride, int& ubase, int& ustride) {
@@ -508,12 +514,13 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
     if constexpr (EARLY) {
      if (el_t < cnt) {
       const unsigned eu = (unsigned)(e0 + el_t);
+      const ElemXYZ exyz = elem_xyz(eu, S.E0, S.E1);
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         xs_lo[a] = xs_hi[a] = -1;
         int pbase, pstride, ubase, ustride;
         line_geometry<n, G::RS>(a, line_t, pbase, pstride, ubase, ustride);
-        const LineTrace t = line_trace<L>(a, eu, line_t, S.E0, S.E1, S.E2, nelem, S.halo_lo[a] != nullptr,
+        const LineTrace t = line_trace<L>(a, eu, exyz, line_t, S.E0, S.E1, S.E2, S.halo_lo[a] != nullptr,
                                           S.halo_hi[a] != nullptr);
         // advection: no flux along a zero-velocity axis, and upwinding zeroes one face
         const bool need_lo = EQ == 1 || (S.vs[a] != real(0) && S.qlo[a] != real(0));
@@ -559,6 +566,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
     }
     // ---- 3. volume + surface terms, axis by axis (FUSED: the last axis applies the stage update
     //         to the finished right-hand side of its line directly) ----
+    const ElemXYZ exyz_t = elem_xyz((unsigned)(e0 + el_t), S.E0, S.E1);  // this thread's element
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const bool last = FUSED && a == DIM - 1;
@@ -613,7 +621,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
               if (has_lo) xlo = xs_lo[a] >= 0 ? sU[xs_lo[a]] : xr_lo[a][0];
               if (has_hi) xhi = xs_hi[a] >= 0 ? sU[xs_hi[a]] : xr_hi[a][0];
             } else {
-              const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), line, S.E0, S.E1, S.E2, nelem,
+              const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), exyz_t, line, S.E0, S.E1, S.E2,
                                                 S.halo_lo[a] != nullptr, S.halo_hi[a] != nullptr);
               if (has_lo)
                 xlo = t.lo_halo ? S.halo_lo[a][t.hoff]
@@ -654,7 +662,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
               xhi[v] = xs_hi[a] >= 0 ? sU[v * epb * SPE + xs_hi[a]] : xr_hi[a][v];
             }
           } else {
-            const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), line, S.E0, S.E1, S.E2, nelem,
+            const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), exyz_t, line, S.E0, S.E1, S.E2,
                                               S.halo_lo[a] != nullptr, S.halo_hi[a] != nullptr);
             const bool lo_in = !t.lo_halo && t.elo >= e0 && t.elo < e0 + cnt;
             const bool hi_in = !t.hi_halo && t.ehi >= e0 && t.ehi < e0 + cnt;
