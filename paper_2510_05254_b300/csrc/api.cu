@@ -292,6 +292,18 @@ int group_upload(Group& g, cudaStream_t stream) {
   return NDG_OK;
 }
 
+// After the stream has been synchronised: NDG_ECUDA if a stage kernel of the group flagged a
+// bulk-copy wait that ran out (the state is then not valid), else NDG_OK.
+int group_check(const Group& g) {
+  if (!g.d_hdr) return NDG_OK;
+  int err = 0;
+  cudaError_t e = cudaMemcpy(&err, &g.d_hdr->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "group status");
+  if (err == kStageErrBulkWait)
+    return fail(NDG_ECUDA, "stage kernel: a bulk copy into shared memory did not complete within the wait limit");
+  return NDG_OK;
+}
+
 void group_free(Group& g, cudaStream_t stream) {
   dev_free(g.d_desc, stream);
   dev_free(g.d_hdr, stream);
@@ -760,7 +772,8 @@ int ndg_synchronize(ndg_ctx* c) {
   if (!c) return fail(NDG_EINVAL, "NULL context");
   DeviceGuard dg(c->cfg.device);
   cudaError_t e = cudaStreamSynchronize(c->stream);
-  return e == cudaSuccess ? NDG_OK : cuda_fail(e, "synchronize");
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  return group_check(c->group);
 }
 
 static int ensure_scratch(ndg_ctx* c) {
@@ -819,7 +832,7 @@ int ndg_get_state(ndg_ctx* c, void* dst, size_t nbytes, int dst_on_device, int l
   }
   if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "get_state copy");
-  return NDG_OK;
+  return dst_on_device ? NDG_OK : group_check(c->group);
 }
 
 int ndg_step(ndg_ctx* c, double dt, int nsteps, int rk) {
@@ -893,6 +906,7 @@ int ndg_norms(ndg_ctx* c, const void* ref, int ref_on_device, ndg_norms_t* out) 
     e = cudaMemcpyAsync(c->h_result, c->d_result, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "norms");
+  if (int rc = group_check(c->group)) return rc;
   const double* r = c->h_result;
   out->l2 = r[0];
   out->linf = r[1];

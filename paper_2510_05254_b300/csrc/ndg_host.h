@@ -36,6 +36,7 @@ struct Group {
   size_t cap = 0;
 };
 int group_upload(Group& g, cudaStream_t stream);
+int group_check(const Group& g);  // after a stream sync: a stage kernel's wait that ran out
 void group_free(Group& g, cudaStream_t stream);
 // Capture one RK step of scheme rk (all stages) of the groups, as parallel branches.
 int capture_step(const std::vector<Group*>& groups, int rk, cudaStream_t cap, cudaGraphExec_t* out);

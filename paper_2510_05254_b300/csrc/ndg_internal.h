@@ -81,7 +81,9 @@ struct GroupHeader {
   int ntiles;
   int epb;                // elements per CTA tile
   int variant;            // kernel mapping: kLineKernel or kLineVarKernel
+  int err;                // set by a stage kernel whose bulk-copy wait ran out (0 otherwise)
 };
+constexpr int kStageErrBulkWait = 1;
 
 // Thread mappings of one stage (identical arithmetic, bitwise-identical results):
 // kLineKernel: one thread per line of n nodes for all variables (fewest FP64 operations);

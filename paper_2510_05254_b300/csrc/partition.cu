@@ -358,7 +358,8 @@ int ndg_partition_get_state(ndg_partition* P, void* dst, size_t nbytes, int dst_
   cudaError_t e = cudaMemcpyAsync(dst, P->d_global, nbytes,
                                   dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
-  return e == cudaSuccess ? NDG_OK : cuda_fail(e, "state copy");
+  if (e != cudaSuccess) return cuda_fail(e, "state copy");
+  return group_check(P->group);
 }
 
 int ndg_partition_step(ndg_partition* P, double dt, int nsteps, int rk) {
@@ -437,6 +438,7 @@ int ndg_partition_norms(ndg_partition* P, ndg_norms_t* out) {
     out->max_speed = std::max(out->max_speed, r.max_speed);
     out->nonfinite += r.nonfinite;
   }
+  if (int rc = group_check(P->group)) return rc;
   out->l2 = std::sqrt(l2sq);
   out->t = P->t;
   out->steps = P->steps;

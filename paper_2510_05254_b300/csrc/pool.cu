@@ -94,6 +94,7 @@ struct ndg_pool {
   std::string worker_error;
   // batching state (worker thread only)
   std::map<long long, PoolClass> classes;
+  unsigned long long steps_checked = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_dirty = true;
   std::deque<cudaEvent_t> inflight;  // events of launched steps (bounded look-ahead)
@@ -294,6 +295,13 @@ void worker_main(ndg_pool* p) {
       cudaEventSynchronize(p->inflight.front());
       cudaEventDestroy(p->inflight.front());
       p->inflight.pop_front();
+      // every 32 steps: did a stage kernel flag a bulk-copy wait that ran out?
+      if ((++p->steps_checked & 31) == 0)
+        for (auto& kv : p->classes)
+          if (group_check(kv.second.group) != NDG_OK) {
+            std::lock_guard<std::mutex> lk(p->mu);
+            p->worker_error = ndg_last_error();
+          }
     }
   }
   while (!p->inflight.empty()) {

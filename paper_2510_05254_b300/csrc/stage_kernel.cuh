@@ -149,6 +149,45 @@ __device__ __forceinline__ void cp_async_elem(real* smem_dst, const real* gmem_s
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+// Bulk (TMA) copies of contiguous global blocks into shared memory, completed on an mbarrier
+// that counts the bytes: one thread arms the barrier with the total and issues the copies, every
+// thread waits for the phase.  The wait is bounded: it gives up after kBulkWaitTries polls (each
+// of which may suspend the thread for a while), and the caller then reports the failure.
+constexpr int kBulkWaitTries = 1 << 22;
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(s) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(s), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_copy(void* smem_dst, const void* gmem_src, unsigned bytes,
+                                          unsigned long long* bar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+               "l"(gmem_src), "r"(bytes), "r"(b)
+               : "memory");
+}
+// true once the barrier's phase of the given parity has completed; false if the polls ran out
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
+  for (int i = 0; i < kBulkWaitTries; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(s), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
 __device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
@@ -396,6 +435,10 @@ struct StageGeom {
   static constexpr bool VEC = sizeof(real) == 4 && DIM == 2 && (n == 8 || n == 4);
   static constexpr bool DENSE = sizeof(real) == 4 && DIM == 3 && n == 6;
   static constexpr bool QUAD = VEC || DENSE;  // copy and update in 16-byte units
+  // BULK (with DENSE): the tile of every variable is one contiguous block in global and shared
+  // memory (elements of 6^3 FP32 values, 864 bytes, a multiple of 16), copied by one bulk (TMA)
+  // copy per variable
+  static constexpr bool BULK = DENSE;
   static constexpr int XW = VEC ? 4 : (DENSE ? 2 : 1);  // x-line access width (floats)
   static constexpr int RS = VEC ? (n == 8 ? 12 : 4) : (DENSE ? n : n + 1);
   static constexpr int SPE = VEC ? (n == 8 ? 104 : 20) : RS * L;  // shared slots per element
@@ -446,6 +489,14 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
   const StagePlan& plan = args.plan;
+  // BULK: the mbarrier of the tile copies, after the arrays (16-byte aligned)
+  unsigned long long* const mbar = reinterpret_cast<unsigned long long*>(
+      smem_raw + (((size_t)G::NS * SPE + (size_t)G::NB * NPE) * epb * sizeof(real) + 15) / 16 * 16);
+  if constexpr (G::BULK) {
+    if (tid == 0) mbar_init(mbar);
+    __syncthreads();
+  }
+  unsigned bulk_phase = 0;
 
   SolveRegs<DIM, real> S;
   for (int tile = blockIdx.x; tile < hdr.ntiles; tile += gridDim.x) {
@@ -476,6 +527,8 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
             const int el = row / L, r = row - el * L;
             cp_async_16(dst + el * SPE + r * G::RS + 4 * c, src + 4 * q);
           }
+        } else if constexpr (G::BULK) {
+          // one bulk copy per variable, issued by thread 0 below
         } else if constexpr (G::DENSE) {
           for (int q = tid; q < total / 4; q += nthr) cp_async_16(dst + 4 * q, src + 4 * q);
         } else {
@@ -549,6 +602,25 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
         }
       }
      }
+    }
+    if constexpr (G::BULK) {
+      if (tid == 0) {
+        // order this CTA's earlier generic accesses to sU before the asynchronous writes
+        fence_proxy_async_smem();
+        const unsigned bytes = (unsigned)(cnt * NPE * sizeof(real));  // 864-byte elements: 16-byte multiple
+        mbar_expect_tx(mbar, bytes * NV);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) bulk_copy(sU + v * epb * SPE, uin + v * vstride + e0 * NPE, bytes, mbar);
+      }
+      const bool ok = mbar_wait(mbar, bulk_phase);
+      if (!__syncthreads_and(ok)) {
+        // the copies did not land in time: flag the group for the host, give the copies in flight
+        // one more bounded wait, and leave
+        if (tid == 0) atomicExch(&const_cast<GroupHeader*>(args.hdr)->err, kStageErrBulkWait);
+        mbar_wait(mbar, bulk_phase);
+        return;
+      }
+      bulk_phase ^= 1u;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -848,6 +920,7 @@ void stage_shape(int epb, int* threads, size_t* smem) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   *threads = epb * G::TPE;
   *smem = ((size_t)G::NS * G::SPE + (size_t)G::NB * G::NPE) * epb * sizeof(real);
+  if constexpr (G::BULK) *smem = (*smem + 15) / 16 * 16 + 16;  // + the bulk copies' mbarrier
 }
 
 }  // namespace ndg
