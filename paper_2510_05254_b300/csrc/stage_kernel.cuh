@@ -11,17 +11,24 @@
 // Euler alpha = max(|u_a^-|, |u_a^+|) + c.  The stage update applies the Butcher tableau of
 // Eq. (RK3)/(RK4)/(RK6) as described by StagePlan.
 //
+// With the exact mass matrix (EXACT instantiations) the two lift terms reach every node of the
+// line through M^-1 e_0 and M^-1 e_N instead of 1/w_0 and 1/w_N at the ends.
+//
 // Work decomposition: a CTA owns a tile of `epb` consecutive elements (in the element layout a
 // contiguous chunk of every variable).  Phases, separated by __syncthreads:
-//   1. copy the tile of the stage input into shared memory (x-lines padded by one slot);
-//   2. Euler: velocities u_a = m_a / rho per node into shared memory;
+//   1. copy the tile of the stage input into shared memory: cp.async into the padded layout
+//      (x-lines one slot apart), 16-byte cp.async into the aligned FP32 2D layout, or one TMA
+//      bulk copy per variable into the unpadded FP32 3D layout (see StageGeom);
+//   2. Euler, FP64: velocities u_a = m_a / rho per node into shared memory (FP32 recomputes them
+//      per line);
 //   3. for each axis a: one thread per line of n nodes evaluates the flux along the line,
 //      applies D by its even-odd halves (D is centro-antisymmetric on LGL nodes), adds the
 //      lifted face terms at the two ends (neighbour traces from shared memory when the
 //      neighbour element is in the tile, else from global memory / L2), and accumulates into
 //      the shared right-hand side;
-//   4. node-parallel stage update with coalesced global reads/writes (2D FP64: fused into the
-//      y-line pass instead, each thread updating the nodes of its line).
+//   4. node-parallel stage update with coalesced global reads/writes, four nodes per step in the
+//      FP32 16-byte layouts (2D FP64: fused into the y-line pass instead, each thread updating
+//      the nodes of its line).
 // The grid is persistent: CTAs loop over the tiles of every solve of the launch.
 #pragma once
 
