@@ -80,3 +80,29 @@ def test_partition_argument_errors():
         assert ei.value.status == nat.NDG_ESTATE
     finally:
         nat.ndg_partition_destroy(part)
+
+
+@pytest.mark.parametrize("dim,N,E,eq,parts", [(2, 7, (6, 5), 1, (2, 2)), (3, 5, (4, 3, 4), 1, (2, 1, 2))])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_partitioned_exact_mass(dim, N, E, eq, parts, dtype):
+    """The exact-mass variant through the partition emulation: bitwise the unpartitioned solve."""
+    p = orc.Problem(dim=dim, degree=N, elems=E + (1,) * (3 - dim), equation=eq, flux=1,
+                    length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3), mass=orc.MASS_EXACT)
+    U = initial(p).astype(np.float64 if dtype == "f64" else np.float32)
+    dt = 0.5 * orc.stable_dt(p, U.astype(np.float64), 0.2)
+    s = Solver(dim, N, E, equation=eq, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3), dtype=dtype,
+               mass=nat.NDG_MASS_EXACT)
+    s.set_state(U)
+    s.step(dt, 2, 4)
+    ref = s.get_state()
+    cfg = _cfg(dim, N, E, eq, dtype)
+    cfg.mass = nat.NDG_MASS_EXACT
+    part = nat.ndg_partition_create(cfg, parts)
+    try:
+        nat.ndg_partition_set_state(part, U.ctypes.data, U.nbytes, False)
+        nat.ndg_partition_step(part, dt, 2, 4)
+        out = np.empty_like(U)
+        nat.ndg_partition_get_state(part, out.ctypes.data, out.nbytes, False)
+        assert np.array_equal(out, ref)
+    finally:
+        nat.ndg_partition_destroy(part)

@@ -123,3 +123,29 @@ def test_pool_status_codes():
         assert ei.value.status == nat.NDG_EINVAL
     finally:
         nat.ndg_pool_destroy(pool)
+
+
+def test_pool_keeps_exact_and_lumped_mass_apart():
+    """Solves that differ only in the mass matrix are separate kernel classes in the pool: each
+    result equals its own solve alone."""
+    pool = nat.ndg_pool_create(4 << 30)
+    try:
+        U, dt = _spec_state(2, 5, (20, 16), 1, "f64", seed=7)
+        g = np.random.default_rng(3)
+        U = U + 0.01 * g.standard_normal(U.shape)  # faces jump: the two lifts differ
+        tickets = []
+        for mass in (nat.NDG_MASS_EXACT, nat.NDG_MASS_LUMPED, nat.NDG_MASS_EXACT):
+            cfg = _cfg(2, 5, (20, 16), 1, "f64")
+            cfg.mass = mass
+            tickets.append((nat.ndg_pool_submit(pool, cfg, U.ctypes.data, U.nbytes, 4, dt, 15), mass))
+        for t, mass in tickets:
+            out = np.empty_like(U)
+            rc, _ = nat.ndg_pool_poll(pool, t, out.ctypes.data, out.nbytes, 60.0)
+            assert rc == nat.NDG_OK
+            s = Solver(2, 5, (20, 16), equation=1, velocity=(1.0, 0.5, 0.25), mass=mass)
+            s.set_state(U)
+            s.step(dt, 15, 4)
+            assert np.array_equal(out, s.get_state())
+            s.close()
+    finally:
+        nat.ndg_pool_destroy(pool)
