@@ -61,6 +61,10 @@ def select_workload(name):
 #          4 stages) = 40 flop; 2D isothermal Euler degree 7: 48; 3D isothermal Euler degree 5: 60;
 #   bytes: RK4 array passes per stage 3, 5, 5, 3 -> 4 on average x sizeof(real).
 FLOPS_PER_DOF = {"adv2d": 40.0, "euler2d": 48.0, "euler3d": 60.0}
+# DRAM bytes per stage launch of the bench workload's kernels (mean of the four RK4 stages), from
+# one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum (command and per-stage values in
+# profiles/stage_kernel_2d_advection_deg7_256x256.md); to be captured again when the kernel changes.
+TRAFFIC_PER_LAUNCH = {("adv2d", "f64"): 92.18e6, ("adv2d", "f32"): 37.79e6}
 FLOPS_PER_DOF_STAGE = FLOPS_PER_DOF["adv2d"]
 PASSES_PER_STAGE = 4.0
 
@@ -462,13 +466,19 @@ def run_ours(args, world, rank, dev, pg):
                 "d2h_bytes_per_step": nb + 8 * 8},
         "gpu_launches": args.steps * (NSTEPS * STAGES + 2),  # per variant timed region
         "roofline": {"bound": "alu", "achieved": ach64, "peak": p64, "unit": "TFLOP/s", "frac": ach64 / p64,
-                     "traffic": None, "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},double>",
+                     "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, "f64")) if not args.elems else None,
+                     "traffic_note": "DRAM bytes per stage launch (ncu, mean of the 4 RK4 stages); algorithmic "
+                                     "%.1f MB: part of the 4 x %.1f MB arrays stays in L2" % (
+                                         PASSES_PER_STAGE * 8 * r64["ndof"] / 1e6, 8 * r64["ndof"] / 1e6),
+                     "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},double>",
                      "peak_note": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop at the max SM clock (derived)",
                      "stage_ms": r64["stage_ms"], "elems_per_block": r64["epb"],
                      "mapping": r64["kernel"]},
         "f32": {"value": value32, "unit": "DOF-updates/s", "ms_per_step": t32 / args.steps,
                 "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
-                             "frac": ach32 / hbm, "traffic": None, "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},float>",
+                             "frac": ach32 / hbm,
+                             "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, "f32")) if not args.elems else None,
+                             "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},float>",
                              "peak_kind": peak_kind, "stage_ms": r32["stage_ms"],
                              "elems_per_block": r32["epb"], "mapping": r32["kernel"],
                              "note": ("working set 4 x %.1f MB %s the 126 MB L2" % (
