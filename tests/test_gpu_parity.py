@@ -464,7 +464,8 @@ def test_float_float_full_size_config2():
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f64ff"])
 @pytest.mark.parametrize("dim,N,E,vel", [(2, 5, (4, 5), (0.0, 0.7, 0.0)), (3, 3, (3, 2, 3), (0.5, 0.0, -0.3)),
-                                         (3, 2, (2, 3, 2), (0.0, 0.0, 0.9))])
+                                         (3, 2, (2, 3, 2), (0.0, 0.0, 0.9)), (2, 7, (5, 4), (0.0, 0.7, 0.0)),
+                                         (2, 3, (5, 4), (0.6, 0.0, 0.0)), (3, 5, (2, 3, 2), (0.5, 0.0, -0.3))])
 def test_advection_with_zero_velocity_components(dim, N, E, vel, dtype):
     """An axis without velocity carries no flux: the kernel skips it (axis 0 included)."""
     p, s = make(dim, N, E, 0, dtype=dtype, epb=3, velocity=vel)
