@@ -68,3 +68,38 @@ def test_no_device_is_reported_as_cuda_error():
     with pytest.raises(nat.NdgError) as ei:
         nat.ndg_create(2, 3, (4, 4), nat.NDG_ADVECTION, nat.NDG_FLUX_UPWIND)
     assert ei.value.status == nat.NDG_ECUDA
+
+
+def _header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/ndg.h, in order."""
+    import re
+    text = open(HEADER).read()
+    m = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", text)
+    assert m, name
+    fields = []
+    for line in m.group(1).splitlines():
+        line = line.split("/*")[0].strip()
+        if not line.endswith(";"):
+            continue
+        decl = line[:-1].replace("*", " ").split()[-1]
+        fields.append(decl.split("[")[0])
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("ndg_config", "ndg_config"), ("ndg_norms_t", "ndg_norms_t"),
+                                          ("ndg_info_t", "ndg_info_t"), ("ndg_solve_stats_t", "ndg_solve_stats_t")])
+def test_binding_structs_match_the_header(cname, pyname):
+    assert [f[0] for f in getattr(nat, pyname)._fields_] == _header_struct_fields(cname)
+
+
+def test_mass_option_is_checked_without_a_device():
+    lib = nat.load()
+    h = ctypes.c_void_p()
+    cfg = nat.ndg_config_init()
+    assert cfg.mass == nat.NDG_MASS_LUMPED
+    cfg.mass = 2
+    assert lib.ndg_create_ex(ctypes.byref(cfg), ctypes.byref(h)) == nat.NDG_EINVAL
+    assert "mass" in nat.ndg_last_error()
+    cfg.mass = nat.NDG_MASS_EXACT
+    cfg.dtype = nat.NDG_F64_FF
+    assert lib.ndg_create_ex(ctypes.byref(cfg), ctypes.byref(h)) == nat.NDG_EINVAL
