@@ -436,11 +436,11 @@ struct StageGeom {
   // number of 16-byte chunks, so eight threads reading eight rows' chunks hit distinct banks;
   // element stride SPE = 8 (mod 32) banks for n = 8 (20 for n = 4), so a warp's y-lines in four
   // (eight) elements do too.  Otherwise x-lines are padded by one slot (RS = n + 1).
-  // DENSE (FP32 3D, n = 6): no padding at all -- x-lines read as float2 are conflict-free and y/z
-  // lines conflict less than with padding -- so the tile copy and the update are plain 16-byte
-  // streams over contiguous memory.
+  // DENSE (FP32 2D / 3D, n = 6): no padding at all -- x-lines read as float2 are conflict-free and
+  // y/z lines conflict no more than with padding -- so the tile copy and the update are plain
+  // 16-byte streams over contiguous memory.
   static constexpr bool VEC = sizeof(real) == 4 && DIM == 2 && (n == 8 || n == 4);
-  static constexpr bool DENSE = sizeof(real) == 4 && DIM == 3 && n == 6;
+  static constexpr bool DENSE = sizeof(real) == 4 && DIM >= 2 && n == 6;
   static constexpr bool QUAD = VEC || DENSE;  // copy and update in 16-byte units
   // BULK (with DENSE): the tile of every variable is one contiguous block in global and shared
   // memory (elements of 6^3 FP32 values, 864 bytes, a multiple of 16), copied by one bulk (TMA)
