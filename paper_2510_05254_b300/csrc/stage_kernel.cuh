@@ -346,16 +346,19 @@ __device__ __forceinline__ LineTrace line_trace(int a, unsigned eu, ElemXYZ c, i
   return t;
 }
 
-// (x-lines in shared memory start RS slots apart: RS = n + 1, or a multiple of 4 for 16-byte access)
-template <int n, int RS>
+// (x-lines in shared memory start RS slots apart: RS = n + 1, or a multiple of 4 for 16-byte access;
+// 3D planes of n x-lines start PS slots apart, RS n unless the planes are padded)
+template <int n, int RS, int PS = RS * n>
 __device__ __forceinline__ void line_geometry(int a, int line, int& pbase, int& pstride, int& ubase, int& ustride) {
   if (a == 0) {
-    pbase = RS * line; pstride = 1; ubase = n * line; ustride = 1;
+    if constexpr (PS == RS * n) pbase = RS * line;
+    else pbase = RS * (line % n) + PS * (line / n);
+    pstride = 1; ubase = n * line; ustride = 1;
   } else if (a == 1) {
     const int i = line % n, k = line / n;
-    pbase = i + RS * n * k; pstride = RS; ubase = i + n * n * k; ustride = n;
+    pbase = i + PS * k; pstride = RS; ubase = i + n * n * k; ustride = n;
   } else {
-    pbase = line % n + RS * (line / n); pstride = RS * n; ubase = line; ustride = n * n;
+    pbase = line % n + RS * (line / n); pstride = PS; ubase = line; ustride = n * n;
   }
 }
 
@@ -439,16 +442,22 @@ struct StageGeom {
   // DENSE (FP32 2D / 3D, n = 6): no padding at all -- x-lines read as float2 are conflict-free and
   // y/z lines conflict no more than with padding -- so the tile copy and the update are plain
   // 16-byte streams over contiguous memory.
+  // PLANE (FP32 3D, n = 8): x-lines unpadded (32 bytes, read as float4), planes of 8 x-lines 72
+  // slots apart (= 8 mod 32 banks), so a warp's y-lines (8 x by 4 z) and z-lines (8 x by 4 y)
+  // hit 32 distinct banks; every plane is one contiguous 256-byte block in global and shared
+  // memory.
   static constexpr bool VEC = sizeof(real) == 4 && DIM == 2 && (n == 8 || n == 4);
   static constexpr bool DENSE = sizeof(real) == 4 && DIM >= 2 && n == 6;
-  static constexpr bool QUAD = VEC || DENSE;  // copy and update in 16-byte units
-  // BULK (with DENSE): the tile of every variable is one contiguous block in global and shared
-  // memory (elements of 6^3 FP32 values, 864 bytes, a multiple of 16), copied by one bulk (TMA)
-  // copy per variable
-  static constexpr bool BULK = DENSE;
-  static constexpr int XW = VEC ? 4 : (DENSE ? 2 : 1);  // x-line access width (floats)
-  static constexpr int RS = VEC ? (n == 8 ? 12 : 4) : (DENSE ? n : n + 1);
-  static constexpr int SPE = VEC ? (n == 8 ? 104 : 20) : RS * L;  // shared slots per element
+  static constexpr bool PLANE = sizeof(real) == 4 && DIM == 3 && n == 8;
+  static constexpr bool QUAD = VEC || DENSE || PLANE;  // copy and update in 16-byte units
+  // BULK (with DENSE and PLANE): the tile is copied by bulk (TMA) copies: DENSE, one per variable
+  // (the tile of a variable is one contiguous block in global and shared memory: elements of 6^3
+  // FP32 values, 864 bytes, a multiple of 16); PLANE, one per 256-byte plane
+  static constexpr bool BULK = DENSE || PLANE;
+  static constexpr int XW = (VEC || PLANE) ? 4 : (DENSE ? 2 : 1);  // x-line access width (floats)
+  static constexpr int RS = VEC ? (n == 8 ? 12 : 4) : ((DENSE || PLANE) ? n : n + 1);
+  static constexpr int PS = PLANE ? n * n + 8 : RS * n;  // plane stride (3D)
+  static constexpr int SPE = VEC ? (n == 8 ? 104 : 20) : (PLANE ? n * PS : RS * L);  // shared slots per element
   // FP64 (arithmetic-bound) stages U^n and ACC in shared memory and keeps the Euler velocities
   // there; FP32 (memory-bound) keeps shared memory small for occupancy: U^n / ACC are
   // prefetched into L2 and read directly, velocities are recomputed per line.
@@ -460,10 +469,17 @@ struct StageGeom {
   static constexpr int NB = SLIM ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
   static constexpr int TPE = VS ? L * NV : L;
-  __device__ static __forceinline__ int pad(int node) { return (node / n) * RS + node % n; }
+  __device__ static __forceinline__ int pad(int node) {
+    if constexpr (PLANE) return node + (PS - n * n) * (node / (n * n));
+    return (node / n) * RS + node % n;
+  }
   // shared slot of the first of four consecutive nodes (QUAD: quad q of the tile)
   __device__ static __forceinline__ int quad_slot(int q) {
     if constexpr (DENSE) return 4 * q;
+    if constexpr (PLANE) {
+      const int el = q / (NPE / 4);
+      return el * SPE + pad(4 * (q - el * (NPE / 4)));
+    }
     const int el = q / (NPE / 4), node = 4 * (q - el * (NPE / 4));
     return el * SPE + (node / n) * RS + node % n;
   }
@@ -579,7 +595,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
       for (int a = 0; a < DIM; ++a) {
         xs_lo[a] = xs_hi[a] = -1;
         int pbase, pstride, ubase, ustride;
-        line_geometry<n, G::RS>(a, line_t, pbase, pstride, ubase, ustride);
+        line_geometry<n, G::RS, G::PS>(a, line_t, pbase, pstride, ubase, ustride);
         const LineTrace t = line_trace<L>(a, eu, exyz, line_t, S.E0, S.E1, S.E2, S.halo_lo[a] != nullptr,
                                           S.halo_hi[a] != nullptr);
         // advection: no flux along a zero-velocity axis, and upwinding zeroes one face
@@ -611,13 +627,26 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
      }
     }
     if constexpr (G::BULK) {
-      if (tid == 0) {
+      if (tid < 32) {
         // order this CTA's earlier generic accesses to sU before the asynchronous writes
         fence_proxy_async_smem();
-        const unsigned bytes = (unsigned)(cnt * NPE * sizeof(real));  // 864-byte elements: 16-byte multiple
-        mbar_expect_tx(mbar, bytes * NV);
+        const unsigned bytes = (unsigned)(cnt * NPE * sizeof(real));  // 864 / 2048-byte elements
+        if (tid == 0) mbar_expect_tx(mbar, bytes * NV);
+        if constexpr (G::PLANE) {
+          // one copy per plane, spread over the first warp (after the expected byte count is set)
+          __syncwarp();
+          constexpr unsigned kPlane = n * n * sizeof(real);
+          const int planes = cnt * n;
+          for (int k = tid; k < NV * planes; k += 32) {
+            const int v = k / planes, pl = k - v * planes;
+            const int el = pl / n, z = pl - el * n;
+            bulk_copy(sU + (v * epb + el) * SPE + z * G::PS, uin + v * vstride + e0 * NPE + pl * (n * n), kPlane,
+                      mbar);
+          }
+        } else if (tid == 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) bulk_copy(sU + v * epb * SPE, uin + v * vstride + e0 * NPE, bytes, mbar);
+          for (int v = 0; v < NV; ++v) bulk_copy(sU + v * epb * SPE, uin + v * vstride + e0 * NPE, bytes, mbar);
+        }
       }
       const bool ok = mbar_wait(mbar, bulk_phase);
       if (!__syncthreads_and(ok)) {
@@ -656,7 +685,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
       const int vsel = rem / L;  // the variable this thread owns (VS), else 0
       if (el < cnt) {
         int pbase, pstride, ubase, ustride;
-        line_geometry<n, G::RS>(a, line, pbase, pstride, ubase, ustride);
+        line_geometry<n, G::RS, G::PS>(a, line, pbase, pstride, ubase, ustride);
         const real* sUe = sU + el * SPE + pbase;
         real* sRe = sR + el * SPE + pbase;
         const real vs = S.vs[a];

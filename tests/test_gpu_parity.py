@@ -134,11 +134,12 @@ def test_tile_size_does_not_change_results_bitwise(epb):
     assert np.array_equal(got, s2.get_state())
 
 
-# (2, 7) and (2, 3) take the FP32 kernel's 16-byte-aligned 2D layout, (3, 5) its unpadded 3D
-# layout with shared trace slots; the others the padded layout
+# (2, 7) and (2, 3) take the FP32 kernel's 16-byte-aligned 2D layout, (2, 5) and (3, 5) its
+# unpadded layout with bulk tile copies, (3, 7) its plane-padded 3D layout with one bulk copy per
+# plane; the others the padded layout
 @pytest.mark.parametrize("dim,N,E,eq", [(1, 3, (11,), 0), (2, 7, (6, 5), 0), (2, 7, (6, 5), 1), (2, 5, (5, 4), 1),
                                         (2, 3, (7, 5), 1), (3, 3, (3, 3, 2), 1), (3, 5, (3, 2, 3), 1),
-                                        (3, 5, (2, 3, 3), 0)])
+                                        (3, 5, (2, 3, 3), 0), (3, 7, (3, 2, 3), 1), (3, 7, (2, 3, 2), 0)])
 def test_fp32_path(dim, N, E, eq):
     p, s = make(dim, N, E, eq, dtype="f32", epb=4)
     U = initial(p)
@@ -391,7 +392,7 @@ def test_torch_allocator_hook():
 @pytest.mark.parametrize("kernel", [nat.NDG_KERNEL_LINE, nat.NDG_KERNEL_LINE_VAR])
 @pytest.mark.parametrize("dim,N,E,eq", [(1, 4, (7,), 1), (2, 7, (5, 3), 0), (2, 6, (4, 3), 1), (2, 3, (6, 5), 1),
                                         (3, 2, (3, 2, 3), 1), (3, 5, (2, 2, 3), 0), (3, 3, (2, 3, 2), 1),
-                                        (3, 5, (2, 3, 2), 1), (2, 7, (5, 4), 1)])
+                                        (3, 5, (2, 3, 2), 1), (2, 7, (5, 4), 1), (3, 7, (2, 2, 3), 1)])
 def test_both_kernel_mappings(kernel, dim, N, E, eq):
     """Thread per line (all variables) and thread per (line, variable): FP64 within 1e-12 per
     step (RK4 and RK6), FP32 within its tolerance, with tiles that leave a ragged end; and the
