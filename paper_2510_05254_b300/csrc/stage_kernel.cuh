@@ -728,6 +728,12 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
             if constexpr (EARLY) {
               if (has_lo) xlo = xs_lo[a] >= 0 ? sU[xs_lo[a]] : xr_lo[a][0];
               if (has_hi) xhi = xs_hi[a] >= 0 ? sU[xs_hi[a]] : xr_hi[a][0];
+            } else if (S.halo_lo[a] == nullptr && S.halo_hi[a] == nullptr) {
+              // no partition halo on this axis: both traces from global memory (the stage input
+              // is read-only during the stage), whether or not the neighbour is in the tile
+              const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), exyz_t, line, S.E0, S.E1, S.E2, false, false);
+              if (has_lo) xlo = uin[t.elo * NPE + ubase + N * ustride];
+              if (has_hi) xhi = uin[t.ehi * NPE + ubase];
             } else {
               const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), exyz_t, line, S.E0, S.E1, S.E2,
                                                 S.halo_lo[a] != nullptr, S.halo_hi[a] != nullptr);
@@ -768,6 +774,17 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
             for (int v = 0; v < NV; ++v) {
               xlo[v] = xs_lo[a] >= 0 ? sU[v * epb * SPE + xs_lo[a]] : xr_lo[a][v];
               xhi[v] = xs_hi[a] >= 0 ? sU[v * epb * SPE + xs_hi[a]] : xr_hi[a][v];
+            }
+          } else if (S.halo_lo[a] == nullptr && S.halo_hi[a] == nullptr) {
+            // no partition halo on this axis: every trace from global memory (the stage input is
+            // read-only during the stage), whether or not the neighbour is in the tile
+            const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), exyz_t, line, S.E0, S.E1, S.E2, false, false);
+            const real* plo = uin + t.elo * NPE + ubase + N * ustride;
+            const real* phi = uin + t.ehi * NPE + ubase;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              xlo[v] = plo[v * vstride];
+              xhi[v] = phi[v * vstride];
             }
           } else {
             const LineTrace t = line_trace<L>(a, (unsigned)(e0 + el), exyz_t, line, S.E0, S.E1, S.E2,

@@ -18,7 +18,8 @@ from tests.test_gpu_parity import initial  # noqa: E402
 
 CASES = [(1, 4, (11,), 1, (4,)), (2, 5, (12, 9), 0, (3, 2)), (2, 7, (10, 7), 1, (2, 3)),
          (3, 3, (4, 6, 5), 1, (2, 3, 2)), (3, 2, (5, 4, 3), 0, (1, 2, 3)), (2, 3, (9, 8), 1, (2, 3)),
-         (3, 5, (4, 3, 5), 1, (2, 1, 2)), (3, 7, (3, 4, 3), 1, (2, 2, 1))]
+         (3, 5, (4, 3, 5), 1, (2, 1, 2)), (3, 7, (3, 4, 3), 1, (2, 2, 1)),
+         (3, 7, (2, 3, 4), 0, (1, 1, 2))]
 
 
 def _cfg(dim, N, E, eq, dtype):
