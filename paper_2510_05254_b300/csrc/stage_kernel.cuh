@@ -916,14 +916,25 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
       // four consecutive nodes of one x-line per step: float4 shared reads and global accesses
       // (every state array is 256-byte aligned: the allocation paths check)
       const int quads = cnt * NPE / 4;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const real* sRv = sR + v * epb * SPE;
-        const real* sUv = sU + v * epb * SPE;
-        const long long goff = v * vstride + e0 * NPE;
+      if constexpr (DIM == 3) {
+        // quads outside, variables inside: a quad's slot and offset serve every variable
         for (int q = tid; q < quads; q += nthr) {
           const int sl = G::quad_slot(q);
-          stage_update_quad(args, S, si, plan, goff + 4 * q, sRv + sl, sUv + sl);
+          const long long g = e0 * NPE + 4 * q;
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            stage_update_quad(args, S, si, plan, v * vstride + g, sR + v * epb * SPE + sl, sU + v * epb * SPE + sl);
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const real* sRv = sR + v * epb * SPE;
+          const real* sUv = sU + v * epb * SPE;
+          const long long goff = v * vstride + e0 * NPE;
+          for (int q = tid; q < quads; q += nthr) {
+            const int sl = G::quad_slot(q);
+            stage_update_quad(args, S, si, plan, goff + 4 * q, sRv + sl, sUv + sl);
+          }
         }
       }
     } else if constexpr (!FUSED) {
