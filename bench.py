@@ -9,10 +9,11 @@ of every bench step.  FP64 is the headline; the FP32 variant and a mixed serving
 reported beside it; the FP64 CPU oracle (single thread, as it stands) gives the CPU baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-serving]
-                    [--no-workloads] [--workload adv2d|euler2d|euler3d] [--variants f64,f32,f64ff]
+                    [--no-workloads] [--workload adv2d|euler2d|euler3d|euler3d7] [--variants f64,f32,f64ff]
 
-Beside the headline, the line carries a table of the two isothermal Euler problems (2D 512^2 at
-degree 7, 3D 64^3 at degree 5): FP64 and FP32 ms per stage with their roofline fractions.
+Beside the headline, the line carries a table of the isothermal Euler problems (2D 512^2 at
+degree 7, 3D 64^3 at degree 5, 3D 32^3 at degree 7): FP64 and FP32 ms per stage with their
+roofline fractions.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload ("replicas only":
 the solve is not partitioned across GPUs); value = total DOF-updates / max rank time.
@@ -44,6 +45,9 @@ WORKLOADS = {
                 "2D isothermal Euler, 512x512 elements, degree 7, 3 x 4096^2 = 50.3M DOF, RK4, 200 steps"),
     "euler3d": (3, 5, (64, 64, 64), 1, (0.0, 0.0, 0.0), 50,
                 "3D isothermal Euler, 64^3 elements, degree 5, 4 x 384^3 = 226.5M DOF, RK4, 50 steps"),
+    # the eighth-order 3D case (degree 7) at the same size class
+    "euler3d7": (3, 7, (32, 32, 32), 1, (0.0, 0.0, 0.0), 50,
+                 "3D isothermal Euler, 32^3 elements, degree 7 (8^3 LGL nodes), 4 x 256^3 = 67.1M DOF, RK4, 50 steps"),
 }
 DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD = WORKLOADS["adv2d"]
 CFL, RK = 0.1, 4
@@ -59,12 +63,13 @@ def select_workload(name):
 #   flops, 2D advection degree 7: sum-factorised strong-form volume term 2 axes x 8 FMA (32 flop)
 #          + per-axis scaling (3) + lifted face terms (1.5) + stage update (3.5 on average over the
 #          4 stages) = 40 flop; 2D isothermal Euler degree 7: 48; 3D isothermal Euler degree 5: 60;
+#          3D isothermal Euler degree 7: 72 (volume 3 axes x 8 FMA = 48 instead of 3 x 6 = 36);
 #   bytes: RK4 array passes per stage 3, 5, 5, 3 -> 4 on average x sizeof(real).
-FLOPS_PER_DOF = {"adv2d": 40.0, "euler2d": 48.0, "euler3d": 60.0}
+FLOPS_PER_DOF = {"adv2d": 40.0, "euler2d": 48.0, "euler3d": 60.0, "euler3d7": 72.0}
 # DRAM bytes per stage launch of the bench workload's kernels (mean of the four RK4 stages), from
 # one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum (command and per-stage values in
 # profiles/stage_kernel_2d_advection_deg7_256x256.md); to be captured again when the kernel changes.
-TRAFFIC_PER_LAUNCH = {("adv2d", "f64"): 92.18e6, ("adv2d", "f32"): 37.79e6}
+TRAFFIC_PER_LAUNCH = {("adv2d", "f64"): 91.95e6, ("adv2d", "f32"): 37.79e6}
 FLOPS_PER_DOF_STAGE = FLOPS_PER_DOF["adv2d"]
 PASSES_PER_STAGE = 4.0
 
@@ -346,17 +351,17 @@ def run_serving(args, dev):
 
 
 def run_workload_table(dev, peaks):
-    """The other two full-size problems (2D isothermal Euler 512^2 degree 7, 3D isothermal Euler
-    64^3 degree 5): ms per RK4 stage of the autotuned tile in FP64 and FP32, CUDA events around a
-    run of RK4 steps, with the FP64-pipe and HBM roofline fractions.  Their working sets (>= 0.8 GB
-    per array) are far larger than L2."""
+    """The other full-size problems (2D isothermal Euler 512^2 degree 7, 3D isothermal Euler 64^3
+    degree 5, and 32^3 at degree 7): ms per RK4 stage of the autotuned tile in FP64 and FP32, CUDA
+    events around a run of RK4 steps, with the FP64-pipe and HBM roofline fractions.  Their working
+    sets (>= 0.27 GB per array) are larger than L2."""
     import torch
     from paper_2510_05254_b300 import inputs
     from paper_2510_05254_b300.solver import Solver
     hbm = peaks.get("hbm_gbs", 6400.0)
     p64 = fp64_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
     out = {}
-    for name, nsteps in (("euler2d", 25), ("euler3d", 5)):
+    for name, nsteps in (("euler2d", 25), ("euler3d", 5), ("euler3d7", 5)):
         dim, deg, el, eq, vel, _, desc = WORKLOADS[name]
         row = {"workload": desc}
         U0 = None
