@@ -17,15 +17,16 @@
 // Work decomposition: a CTA owns a tile of `epb` consecutive elements (in the element layout a
 // contiguous chunk of every variable).  Phases, separated by __syncthreads:
 //   1. copy the tile of the stage input into shared memory: cp.async into the padded layout
-//      (x-lines one slot apart), 16-byte cp.async into the aligned FP32 2D layout, or one TMA
-//      bulk copy per variable into the unpadded FP32 3D layout (see StageGeom);
+//      (x-lines one slot apart), 16-byte cp.async into the aligned FP32 2D layout, one TMA bulk
+//      copy per variable into the unpadded FP32 degree-5 layout, or one per 256-byte plane into
+//      the plane-padded FP32 3D degree-7 layout (see StageGeom);
 //   2. Euler, FP64: velocities u_a = m_a / rho per node into shared memory (FP32 recomputes them
 //      per line);
 //   3. for each axis a: one thread per line of n nodes evaluates the flux along the line,
 //      applies D by its even-odd halves (D is centro-antisymmetric on LGL nodes), adds the
-//      lifted face terms at the two ends (neighbour traces from shared memory when the
-//      neighbour element is in the tile, else from global memory / L2), and accumulates into
-//      the shared right-hand side;
+//      lifted face terms at the two ends (neighbour traces from global memory / L2, or from a
+//      partition halo; the FP32 degree-7 2D layout and axes with halos read a neighbour inside
+//      the tile from shared memory), and accumulates into the shared right-hand side;
 //   4. node-parallel stage update with coalesced global reads/writes, four nodes per step in the
 //      FP32 16-byte layouts (2D FP64: fused into the y-line pass instead, each thread updating
 //      the nodes of its line).
