@@ -501,6 +501,11 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
   constexpr bool EARLY = DIM <= 2 && !FF;
+  // BPF (FP32, elements a multiple of 16 bytes; Euler or the bulk-copy layouts): the update's
+  // U^n / ACC reach L2 by bulk prefetches (16-byte aligned ranges: the arrays are 256-byte
+  // aligned).  Measured on the 16-byte 2D layouts: Euler degree 7 170 -> 167 us, advection
+  // degree 3 19.6 -> 20.8 us, so advection there keeps the per-line prefetches.
+  constexpr bool BPF = G::SLIM && (NPE * sizeof(real)) % 16 == 0 && (G::BULK || EQ == 1);
   // 2D FP64: the y-line threads own whole lines of finished right-hand side and apply the stage
   // update to them directly (no shared round trip, one barrier less: 2D Euler 2.40 -> 2.28 ms per
   // stage).  Elsewhere the extra registers cost more occupancy than the round trip does (measured:
@@ -567,9 +572,9 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
           }
         }
         if constexpr (G::SLIM) {
-          // start the update's reads now: one L2 prefetch per 128-byte line of U^n / ACC (BULK:
+          // start the update's reads now: one L2 prefetch per 128-byte line of U^n / ACC (BPF:
           // one bulk prefetch per array, below)
-          if constexpr (!G::BULK) {
+          if constexpr (!BPF) {
             constexpr int per_line = 128 / (int)sizeof(real);
             for (int idx = tid * per_line; idx < total; idx += nthr * per_line) {
               if (need_un) asm volatile("prefetch.global.L2 [%0];" ::"l"(S.un + v * vstride + e0 * NPE + idx));
@@ -587,6 +592,20 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
           const real* s3 = S.acc + v * vstride + e0 * NPE;
           real* d3 = sA + v * epb * NPE;
           for (int idx = tid; idx < total; idx += nthr) cp_async_elem(d3 + idx, s3 + idx);
+        }
+      }
+    }
+    if constexpr (BPF) {
+      if (tid == 0) {
+        // this tile's U^n / ACC (read by the update) into L2 by the copy engine: one instruction
+        // per array instead of one prefetch per 128-byte line and thread (measured: FP32 2D Euler
+        // degree 5 244 -> 213 us, 3D Euler degree 7 / 5 270 -> 262 / 1037 -> 999 us; prefetching
+        // the stage input of the CTA's next tile as well made 3D slower)
+        const unsigned bytes = (unsigned)(cnt * NPE * sizeof(real));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if (need_un) bulk_prefetch_l2(S.un + v * vstride + e0 * NPE, bytes);
+          if (need_acc) bulk_prefetch_l2(S.acc + v * vstride + e0 * NPE, bytes);
         }
       }
     }
@@ -669,17 +688,6 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
         } else if (tid == 0) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) bulk_copy(sU + v * epb * SPE, uin + v * vstride + e0 * NPE, bytes, mbar);
-        }
-        if (tid == 0) {
-          // this tile's U^n / ACC (read by the update) into L2 by the copy engine: one instruction
-          // per array instead of one prefetch per 128-byte line and thread (measured: FP32 2D
-          // Euler degree 5 244 -> 213 us, 3D Euler degree 7 / 5 270 -> 262 / 1037 -> 999 us; also
-          // prefetching the stage input of the CTA's next tile made 3D slower)
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            if (need_un) bulk_prefetch_l2(S.un + v * vstride + e0 * NPE, bytes);
-            if (need_acc) bulk_prefetch_l2(S.acc + v * vstride + e0 * NPE, bytes);
-          }
         }
       }
       const bool ok = mbar_wait(mbar, bulk_phase);
