@@ -595,19 +595,20 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
         }
       }
     }
-    if constexpr (BPF) {
-      if (tid == 0) {
-        // this tile's U^n / ACC (read by the update) into L2 by the copy engine: one instruction
-        // per array instead of one prefetch per 128-byte line and thread (measured: FP32 2D Euler
-        // degree 5 244 -> 213 us, 3D Euler degree 7 / 5 270 -> 262 / 1037 -> 999 us; prefetching
-        // the stage input of the CTA's next tile as well made 3D slower)
-        const unsigned bytes = (unsigned)(cnt * NPE * sizeof(real));
+    // this tile's U^n / ACC (read by the update) into L2 by the copy engine: one instruction per
+    // array instead of one prefetch per 128-byte line and thread (measured: FP32 2D Euler degree
+    // 5 244 -> 213 us, 3D Euler degree 7 / 5 270 -> 262 / 1037 -> 999 us; prefetching the stage
+    // input of the CTA's next tile as well made 3D slower).  Issued after the tile's own copies.
+    auto prefetch_update_operands = [&]() {
+      const unsigned bytes = (unsigned)(cnt * NPE * sizeof(real));
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          if (need_un) bulk_prefetch_l2(S.un + v * vstride + e0 * NPE, bytes);
-          if (need_acc) bulk_prefetch_l2(S.acc + v * vstride + e0 * NPE, bytes);
-        }
+      for (int v = 0; v < NV; ++v) {
+        if (need_un) bulk_prefetch_l2(S.un + v * vstride + e0 * NPE, bytes);
+        if (need_acc) bulk_prefetch_l2(S.acc + v * vstride + e0 * NPE, bytes);
       }
+    };
+    if constexpr (BPF && !G::BULK) {
+      if (tid == 0) prefetch_update_operands();
     }
     // ---- 1b. neighbour traces outside the tile: their global / halo loads are issued now, so
     //         they are in flight together with the tile's copies ----
@@ -688,6 +689,9 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
         } else if (tid == 0) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) bulk_copy(sU + v * epb * SPE, uin + v * vstride + e0 * NPE, bytes, mbar);
+        }
+        if constexpr (BPF) {
+          if (tid == 0) prefetch_update_operands();
         }
       }
       const bool ok = mbar_wait(mbar, bulk_phase);
