@@ -182,6 +182,15 @@ def max_over_ranks(pg, x, dev):
     return float(t.item())
 
 
+def data_description():
+    """What the synthetic initial state of the selected workload is."""
+    if EQ == 0:
+        return "synthetic (seeded Gaussian pulse + Fourier noise)"
+    if DIM == 2:
+        return "synthetic (isothermal Euler: density 1 + 0.1 sin sin, seeded smooth shear velocity, Mach <= 0.3)"
+    return "synthetic (isothermal Euler: density 1, Taylor-Green velocity of amplitude 0.1)"
+
+
 def initial_condition(X):
     from paper_2510_05254_b300 import inputs
     if EQ == 0:
@@ -214,11 +223,12 @@ def run_reference(args, world, rank):
         rates.append(r)
         tot += el
     value = statistics.median(rates)
-    sample = f"{sample_steps} RK4 step of the full 4.19M-DOF workload per bench step (1000 in the GPU step)"
+    ndof = config_block(world)["dof"]
+    sample = f"{sample_steps} RK4 step of the full {ndof / 1e6:.2f}M-DOF workload per bench step ({NSTEPS} in the GPU step)"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_block(world),
+            "data": data_description(), "config": config_block(world),
             "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -475,7 +485,7 @@ def run_ours(args, world, rank, dev, pg):
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian pulse + Fourier noise)",
+        "vs_baseline": None, "dtype": "f64", "data": data_description(),
         "config": config_block(world),
         "e2e": {"value": world * work / e2e_s, "unit": "DOF-updates/s", "h2d_bytes_per_step": nb,
                 "d2h_bytes_per_step": nb + 8 * 8},
