@@ -468,9 +468,10 @@ struct StageGeom {
   // there; FP32 (memory-bound) keeps shared memory small for occupancy: U^n / ACC are
   // prefetched into L2 and read directly, velocities are recomputed per line.
   static constexpr bool SLIM = sizeof(real) == 4;
-  // EARLY: neighbour-trace loads issued with the tile copy and a batched stage update (more loads
-  // in flight); it costs registers, and pays only for 1D/2D (measured: 3D and float-float lose
-  // occupancy), so 3D keeps the per-axis trace loads and the one-node-at-a-time update.
+  // EARLY (stage_body): neighbour-trace loads issued with the tile copy and a batched stage
+  // update (more loads in flight); it costs registers, and pays only for 1D/2D (measured: 3D and
+  // float-float lose occupancy), so 3D and float-float load each axis's traces in its pass (and
+  // the FP64 / float-float update there goes one node at a time; FP32 3D moves quads).
   static constexpr int NS = (EQ == 0 || SLIM) ? 2 * NV : 2 * NV + DIM;  // shared arrays of SPE per element
   static constexpr int NB = SLIM ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
