@@ -36,7 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF-updates/s per RK stage (FP64 vs FP32); batched solves/s + p50/p99 latency"
-# The bench workload (default) and the two other full-size problems of the survey, selectable with
+# The bench workload (default) and the other full-size problems, selectable with
 # --workload: (dim, degree, elements, equation, velocity, RK steps per bench step, description).
 WORKLOADS = {
     "adv2d": (2, 7, (256, 256), 0, (1.0, 0.5, 0.0), 1000,
@@ -59,7 +59,7 @@ def select_workload(name):
     global DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD
     DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD = WORKLOADS[name]
 
-# Algorithmic work of one RK4 stage per DOF (see DESIGN.md):
+# Algorithmic work of one RK4 stage per DOF:
 #   flops, 2D advection degree 7: sum-factorised strong-form volume term 2 axes x 8 FMA (32 flop)
 #          + per-axis scaling (3) + lifted face terms (1.5) + stage update (3.5 on average over the
 #          4 stages) = 40 flop; 2D isothermal Euler degree 7: 48; 3D isothermal Euler degree 5: 60;
