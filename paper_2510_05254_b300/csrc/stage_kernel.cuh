@@ -444,7 +444,9 @@ struct StageGeom {
   // x-line passes and the stage update move four values per instruction.  Row stride RS: an odd
   // number of 16-byte chunks, so eight threads reading eight rows' chunks hit distinct banks;
   // element stride SPE = 8 (mod 32) banks for n = 8 (20 for n = 4), so a warp's y-lines in four
-  // (eight) elements do too.  Otherwise x-lines are padded by one slot (RS = n + 1).
+  // (eight) elements do too.  (n = 4: a quarter-warp's float4 rows span two elements and are
+  // 2-way; no element stride serves both them and the y-lines.)  Otherwise x-lines are padded by
+  // one slot (RS = n + 1).
   // DENSE (FP32 2D / 3D, n = 6): no padding at all -- x-lines read as float2 are conflict-free and
   // y/z lines conflict no more than with padding -- so the tile copy and the update are plain
   // 16-byte streams over contiguous memory.
