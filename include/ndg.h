@@ -133,11 +133,13 @@ int ndg_destroy(ndg_ctx* ctx);
 
 /* Copy a state into the context: nbytes must equal info.state_bytes; src is a host pointer
  * (src_on_device = 0; pageable or pinned) or a device pointer (1) of the context's dtype, in
- * `layout`.  Resets t and the step counter.  Async on the context stream for device sources;
- * a host source is fully read before the call returns. */
+ * `layout`.  Resets t and the step counter, and clears the failure flag of earlier steps (see
+ * ndg_synchronize).  Async on the context stream for device sources; a host source is fully
+ * read before the call returns. */
 int ndg_set_state(ndg_ctx* ctx, const void* src, size_t nbytes, int src_on_device, int layout);
 
-/* Copy the current state out (same size/layout rules).  To host: waits for the copy. */
+/* Copy the current state out (same size/layout rules).  To host: waits for the copy, and
+ * returns NDG_ECUDA when the context's failure flag is set (see ndg_synchronize). */
 int ndg_get_state(ndg_ctx* ctx, void* dst, size_t nbytes, int dst_on_device, int layout);
 
 /* Advance nsteps steps of size dt with Runge-Kutta scheme rk (NDG_RK3/4/6; Eq. (RK3), (RK4),
@@ -150,7 +152,8 @@ int ndg_step(ndg_ctx* ctx, double dt, int nsteps, int rk_scheme);
 /* Norms of the state, or of state - ref when ref is not NULL (ref has the context's dtype and
  * element layout, on the host if ref_on_device = 0, else on the device).  FP64 accumulation,
  * deterministic (fixed reduction order, no atomics).  Waits for the result.  Returns
- * NDG_ENONFINITE when the state holds NaN/Inf (out is still filled). */
+ * NDG_ENONFINITE when the state holds NaN/Inf (out is still filled), NDG_ECUDA when the
+ * context's failure flag is set (see ndg_synchronize). */
 int ndg_norms(ndg_ctx* ctx, const void* ref, int ref_on_device, ndg_norms_t* out);
 
 /* Stable time step dt = cfl * h_min / lambda (h_min the smallest physical LGL node spacing,
@@ -171,8 +174,21 @@ int ndg_lgl(int degree, double* xi, double* w);
 /* The stream the context runs on (a cudaStream_t). */
 void* ndg_stream(const ndg_ctx* ctx);
 
-/* Wait for all work queued on the context's stream. */
+/* Wait for all work queued on the context's stream.  Returns NDG_ECUDA when a stage kernel that
+ * stepped this context (alone, in a batch or as a partition block) gave up waiting for its
+ * bulk copies into shared memory: every wait is bounded, and a CTA that gives up leaves tiles
+ * unprocessed, so the state is not valid.  The flag stays set (ndg_get_state and ndg_norms
+ * report it too) until the next ndg_set_state. */
 int ndg_synchronize(ndg_ctx* ctx);
+
+/* Test hook for the failure path above.  With polls > 0, every launch work list uploaded after
+ * the call (contexts created or given a new dt, batch steps, partitions, pool membership
+ * changes) makes the stage kernels that copy their tiles by bulk copies (FP32 degree 5 in
+ * 2D/3D, FP32 degree 7 in 3D) arm their copy barrier without issuing the copies and give up
+ * after `polls` polls, so the bounded wait runs out and the failure flag is raised; nothing is
+ * left in flight.  polls = 0 restores normal operation (the default limit of 2^22 polls).
+ * Process-wide; for tests only.  NDG_EINVAL for polls < 0. */
+int ndg_debug_stall_copies(int polls);
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* ndg_last_error(void);
@@ -209,12 +225,14 @@ int ndg_autotune(ndg_ctx* ctx, int rk_scheme, int* best_epb, double* best_ms);
  *   stream: cudaStream_t to enqueue on (NULL: the legacy default stream).
  * Asynchronous: nothing waits for the GPU.  The per-block partial sums live in one file-scope
  * device array of 1024 x 10 doubles (80 KiB) that every GPU which loads the library keeps until
- * the process exits; no call allocates or frees anything.  The first call on a device looks the
- * array's device address up (cudaGetSymbolAddress) -- make that first call before any stream
+ * the process exits; no call allocates or frees anything.  Every call looks the array's device
+ * address up (cudaGetSymbolAddress, with cfg->device current); on a device's first call that
+ * lookup may load the library's module there -- make that first call before any stream
  * capture.  All calls share the array: each call writes the partials it later reads, so nothing
  * has to start at zero, but calls whose kernels overlap on the GPU (other streams, other host
  * threads) race on it and must be serialised by the caller.  Errors: NDG_EINVAL (bad cfg, NULL
- * U/out, nblocks outside 0..1024), NDG_ECUDA. */
+ * U/out, nblocks outside 0..1024), NDG_ECUDA (this call's launch failed, or an error of earlier
+ * work was already pending: that one is reported and left pending, not cleared). */
 int ndg_norms_noalloc(const ndg_config* cfg, const void* U, const void* ref, int nblocks, double* out,
                       void* stream);
 
@@ -224,7 +242,8 @@ int ndg_norms_noalloc(const ndg_config* cfg, const void* U, const void* ref, int
  * is one persistent stage-kernel launch per stage over all of that class's solves, the classes
  * running as parallel branches.  The contexts stay owned by the caller and must outlive the
  * batch; the batch runs on the first context's stream.  Results are bitwise those of ndg_step on
- * each context alone. */
+ * each context alone.  A failed bulk-copy wait during a batch step raises the failure flag of
+ * every member context (reported by their ndg_synchronize, ndg_get_state and ndg_norms). */
 int ndg_batch_create(ndg_ctx* const* ctxs, int n, ndg_batch** out);
 /* dts[i] is the step of context i; every context advances nsteps steps of scheme rk. */
 int ndg_batch_step(ndg_batch* b, const double* dts, int nsteps, int rk_scheme);
@@ -276,7 +295,9 @@ int ndg_pool_submit(ndg_pool* p, const ndg_config* cfg, const void* u0, size_t n
                     double dt, int nsteps, uint64_t* ticket);
 /* Wait up to timeout_s (0: do not wait) for the solve.  When done, copies the final state to
  * result (host, element layout; NULL to skip), fills stats (may be NULL) and forgets the ticket.
- * NDG_EAGAIN (timeout 0, not done), NDG_ETIMEOUT (waited, not done), NDG_EINVAL (unknown). */
+ * NDG_EAGAIN (timeout 0, not done), NDG_ETIMEOUT (waited, not done), NDG_EINVAL (unknown),
+ * NDG_ECUDA (a stage kernel that stepped this solve gave up waiting for its bulk copies: the
+ * result is not valid; or a CUDA call of the pool failed). */
 int ndg_pool_poll(ndg_pool* p, uint64_t ticket, void* result, size_t nbytes,
                   ndg_solve_stats_t* stats, double timeout_s);
 /* Counters: solves queued, running, finished; device bytes in use; peak device bytes. */

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -73,7 +74,9 @@ ShapeFn pick_shape(const KernelClass& k) {
   static ShapeFn (*t[3][3])(int, int) = {{stage_f64_d1_shape, stage_f64_d2_shape, stage_f64_d3_shape},
                                          {stage_f32_d1_shape, stage_f32_d2_shape, stage_f32_d3_shape},
                                          {stage_f64ff_d1_shape, stage_f64ff_d2_shape, stage_f64ff_d3_shape}};
-  // the exact-mass kernels have the lumped ones' shapes
+  static ShapeFn (*x[2][3])(int, int) = {{stage_f64x_d1_shape, stage_f64x_d2_shape, stage_f64x_d3_shape},
+                                         {stage_f32x_d1_shape, stage_f32x_d2_shape, stage_f32x_d3_shape}};
+  if (k.mass == NDG_MASS_EXACT && k.dtype < 2) return x[k.dtype][k.dim - 1](k.degree, k.equation);
   return t[k.dtype][k.dim - 1](k.degree, k.equation);
 }
 }  // namespace
@@ -271,11 +274,17 @@ struct DeviceGuard {
 
 namespace ndg {
 
+namespace {
+// ndg_debug_stall_copies: the wait limit and the stall switch written into every header upload
+std::atomic<int> g_debug_wait_polls{0};
+}  // namespace
+
 int group_upload(Group& g, cudaStream_t stream) {
   if (g.h_desc.size() > g.cap || !g.d_desc) {
     if (g.d_desc) dev_free(g.d_desc, stream);
     if (!g.d_hdr) {
       cudaError_t e = dev_alloc((void**)&g.d_hdr, sizeof(GroupHeader), stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(g.d_hdr, 0, sizeof(GroupHeader), stream);
       if (e != cudaSuccess) return cuda_fail(e, "alloc group header");
     }
     size_t cap = std::max<size_t>(1, g.h_desc.size());
@@ -283,8 +292,10 @@ int group_upload(Group& g, cudaStream_t stream) {
     if (e != cudaSuccess) return cuda_fail(e, "alloc solve descriptors");
     g.cap = cap;
   }
-  GroupHeader h{(int)g.h_desc.size(), g.ntiles, g.epb, g.variant};
-  cudaError_t e = cudaMemcpyAsync(g.d_hdr, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
+  const int polls = g_debug_wait_polls.load();
+  GroupHeader h{(int)g.h_desc.size(), g.ntiles, g.epb, g.variant, polls, polls > 0 ? 1 : 0, 0, 0};
+  // the fields before `err` only: a flag raised by an earlier launch stays until it is read
+  cudaError_t e = cudaMemcpyAsync(g.d_hdr, &h, kGroupHeaderUpload, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess && !g.h_desc.empty())
     e = cudaMemcpyAsync(g.d_desc, g.h_desc.data(), g.h_desc.size() * sizeof(SolveDesc),
                         cudaMemcpyHostToDevice, stream);
@@ -301,6 +312,17 @@ int group_check(const Group& g) {
   if (e != cudaSuccess) return cuda_fail(e, "group status");
   if (err == kStageErrBulkWait)
     return fail(NDG_ECUDA, "stage kernel: a bulk copy into shared memory did not complete within the wait limit");
+  return NDG_OK;
+}
+
+int status_check(const int* d_status) {
+  if (!d_status) return NDG_OK;
+  int st = 0;
+  cudaError_t e = cudaMemcpy(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "solve status");
+  if (st == kStageErrBulkWait)
+    return fail(NDG_ECUDA, "stage kernel: a bulk copy into shared memory did not complete within the wait limit "
+                           "(the state is not valid until a new one is set)");
   return NDG_OK;
 }
 
@@ -426,6 +448,7 @@ struct ndg_ctx {
   double* d_result = nullptr;
   double* h_result = nullptr;  // pinned
   void* d_scratch = nullptr;   // state-sized scratch (host refs, grid layout)
+  int* d_status = nullptr;     // set by a stage kernel whose bulk-copy wait ran out; cleared by set_state
   std::mutex mu;
 };
 
@@ -563,7 +586,8 @@ bool valid_rk(int rk) { return rk == 3 || rk == 4 || rk == 6; }
 
 SolveDesc ndg_ctx_desc(const ndg_ctx* c) { return c->desc; }
 int ndg_ctx_ensure_buffers(ndg_ctx* c, int rk) { return ensure_buffers(c, rk); }
-void ndg_ctx_mark_state(ndg_ctx* c) {
+void ndg_ctx_mark_state(ndg_ctx* c, cudaStream_t stream) {
+  cudaMemsetAsync(c->d_status, 0, sizeof(int), stream);
   c->have_state = true;
   c->t = 0.0;
   c->steps = 0;
@@ -644,6 +668,7 @@ int ndg_destroy(ndg_ctx* c) {
     dev_free(c->d_partials, c->stream);
     dev_free(c->d_result, c->stream);
     dev_free(c->d_scratch, c->stream);
+    dev_free(c->d_status, c->stream);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -707,7 +732,10 @@ int ndg_create_ex(const ndg_config* cfg, ndg_ctx** out) {
     e = dev_alloc((void**)&c->d_partials, kNormBlocks * kNormFields * sizeof(double), c->stream);
     if (e == cudaSuccess) e = dev_alloc((void**)&c->d_result, kNormFields * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_result, kNormFields * sizeof(double));
+    if (e == cudaSuccess) e = dev_alloc((void**)&c->d_status, 256, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) rc = fail(NDG_ENOMEM, "norm buffers: %s", cudaGetErrorString(e));
+    c->desc.status = c->d_status;
   }
   if (rc == NDG_OK) {
     TileConfig t = tuned_tile(c->kc);
@@ -773,7 +801,7 @@ int ndg_synchronize(ndg_ctx* c) {
   DeviceGuard dg(c->cfg.device);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "synchronize");
-  return group_check(c->group);
+  return status_check(c->d_status);
 }
 
 static int ensure_scratch(ndg_ctx* c) {
@@ -803,6 +831,8 @@ int ndg_set_state(ndg_ctx* c, const void* src, size_t nbytes, int src_on_device,
       e = (cudaError_t)launch_relayout(c->kc.dtype, c->cfg.dim, c->cfg.degree, c->nvar, c->cfg.elems,
                                        c->d_scratch, c->buf[kUN], true, c->stream);
   }
+  // a new state: a flag raised by earlier steps no longer applies
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess && !src_on_device) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
   c->have_state = true;
@@ -832,7 +862,7 @@ int ndg_get_state(ndg_ctx* c, void* dst, size_t nbytes, int dst_on_device, int l
   }
   if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "get_state copy");
-  return dst_on_device ? NDG_OK : group_check(c->group);
+  return dst_on_device ? NDG_OK : status_check(c->d_status);
 }
 
 int ndg_step(ndg_ctx* c, double dt, int nsteps, int rk) {
@@ -906,7 +936,7 @@ int ndg_norms(ndg_ctx* c, const void* ref, int ref_on_device, ndg_norms_t* out) 
     e = cudaMemcpyAsync(c->h_result, c->d_result, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "norms");
-  if (int rc = group_check(c->group)) return rc;
+  if (int rc = status_check(c->d_status)) return rc;
   const double* r = c->h_result;
   out->l2 = r[0];
   out->linf = r[1];
@@ -950,6 +980,12 @@ int ndg_node_coords(ndg_ctx* c, double* X, size_t count) {
       }
     }
   }
+  return NDG_OK;
+}
+
+int ndg_debug_stall_copies(int polls) {
+  if (polls < 0) return fail(NDG_EINVAL, "polls must be >= 0");
+  g_debug_wait_polls.store(polls);
   return NDG_OK;
 }
 

@@ -35,8 +35,14 @@ struct Group {
   GroupHeader* d_hdr = nullptr;
   size_t cap = 0;
 };
+// Upload the work list and the header fields before `err` (the flag is zeroed only when the
+// header is allocated).  The bulk-copy wait limit and the test switch that stalls the copies
+// come from ndg_debug_stall_copies().
 int group_upload(Group& g, cudaStream_t stream);
 int group_check(const Group& g);  // after a stream sync: a stage kernel's wait that ran out
+// After a stream sync: NDG_ECUDA if the device status word a stage kernel sets when its
+// bulk-copy wait runs out (SolveDesc::status) is set, else NDG_OK.
+int status_check(const int* d_status);
 void group_free(Group& g, cudaStream_t stream);
 // Capture one RK step of scheme rk (all stages) of the groups, as parallel branches.
 int capture_step(const std::vector<Group*>& groups, int rk, cudaStream_t cap, cudaGraphExec_t* out);
@@ -54,7 +60,8 @@ TileConfig tuned_tile(const KernelClass& kc);  // epb == 0 when the class was ne
 // its RK buffers for scheme rk, and marking its state as set by a device-side copy.
 SolveDesc ndg_ctx_desc(const ndg_ctx* c);
 int ndg_ctx_ensure_buffers(ndg_ctx* c, int rk);
-void ndg_ctx_mark_state(ndg_ctx* c);
+// Marks the state as set and clears the context's status word (stream-ordered on `stream`).
+void ndg_ctx_mark_state(ndg_ctx* c, cudaStream_t stream);
 
 // Geometry part of a solve descriptor (scales, lift coefficients, element counts).
 void fill_solve_geometry(const ndg_config& cfg, const Basis& b, SolveDesc* d);

@@ -73,17 +73,30 @@ struct SolveDesc {
   // line through it); NULL = periodic wrap inside this solve.
   const void* halo_lo[3];
   const void* halo_hi[3];
+  // Device int of the solve's owner (a context's or a serving slot's status word), or NULL: a
+  // stage kernel whose bulk-copy wait runs out sets it for every solve of the launch (the CTA
+  // that gives up leaves tiles of any of them unprocessed).  Sticky until the owner resets it.
+  int* status;
 };
 
-// Header of a launch's work list (device memory): tiles are numbered across all solves.
+// Header of a launch's work list (device memory): tiles are numbered across all solves.  The
+// host uploads the fields before `err` (kGroupHeaderUpload bytes) whenever the work list
+// changes; `err` is zeroed once when the header is allocated and then written only by the
+// kernels, so a flag raised by one launch survives later uploads until the host reads it.
 struct GroupHeader {
   int nsolves;
   int ntiles;
   int epb;                // elements per CTA tile
   int variant;            // kernel mapping: kLineKernel or kLineVarKernel
+  int wait_polls;         // polls of a bulk-copy wait before it gives up (0: kBulkWaitPolls)
+  int stall_copies;       // test switch: arm the bulk-copy barrier but issue no copy, so the
+                          // wait runs out (nothing is in flight when the kernel leaves); 0 normally
   int err;                // set by a stage kernel whose bulk-copy wait ran out (0 otherwise)
+  int pad;
 };
+constexpr size_t kGroupHeaderUpload = offsetof(GroupHeader, err);
 constexpr int kStageErrBulkWait = 1;
+constexpr int kBulkWaitPolls = 1 << 22;
 
 // Thread mappings of one stage (identical arithmetic, bitwise-identical results):
 // kLineKernel: one thread per line of n nodes for all variables (fewest FP64 operations);

@@ -6,7 +6,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "../../include/ndg.h"
 #include "ndg_host.h"
@@ -149,10 +148,13 @@ int launch_norms(int dtype, int dim, int degree, int equation, const void* U, co
   a.adv_speed = 0.0;
   for (int d = 0; d < dim; ++d) a.adv_speed += std::fabs(velocity[d]);
   cudaStream_t s = (cudaStream_t)stream;
+  // an error left pending by earlier work (possibly the caller's) is reported, not cleared
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) return (int)pending;
   if (dtype_bytes(dtype) == 8) norms_partial<double><<<nblocks, 256, 0, s>>>(a, partials);
   else norms_partial<float><<<nblocks, 256, 0, s>>>(a, partials);
   norms_final<<<1, 32, 0, s>>>(partials, nblocks, a.adv_speed, equation, result);
-  return (int)cudaGetLastError();
+  return (int)cudaGetLastError();  // this call's launch error
 }
 
 int launch_relayout(int dtype, int dim, int degree, int nvar, const int* E, const void* src,
@@ -190,21 +192,15 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * n
 namespace ndg {
 namespace {
 
-// Device address of g_noalloc_partials, looked up once per device with that device current.
-// In host code the symbol names a host-side stand-in, never the device memory itself.
-std::mutex g_noalloc_mu;
-double* g_noalloc_addr[64] = {nullptr};
-
-int noalloc_scratch(int device, double** out) {
-  if (device < 0 || device >= 64) return fail(NDG_EINVAL, "device ordinal %d out of range", device);
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[device]) {
-    double* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static norms scratch");
-    g_noalloc_addr[device] = p;
-  }
-  *out = g_noalloc_addr[device];
+// Device address of g_noalloc_partials on the current device.  In host code the symbol names a
+// host-side stand-in, never the device memory itself, so the address is looked up (with the
+// device current) on every call: cheap once the module is loaded, and never stale -- a cached
+// address would dangle after a cudaDeviceReset reloads the module.
+int noalloc_scratch(double** out) {
+  double* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static norms scratch");
+  *out = p;
   return NDG_OK;
 }
 
@@ -228,7 +224,9 @@ extern "C" int ndg_norms_noalloc(const ndg_config* cfg, const void* U, const voi
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   }
   double* scratch = nullptr;
-  rc = noalloc_scratch(cfg->device, &scratch);
+  const cudaError_t pending = cudaPeekAtLastError();
+  rc = pending == cudaSuccess ? noalloc_scratch(&scratch)
+                              : cuda_fail(pending, "an error of earlier work is pending (reported, not cleared)");
   if (rc == NDG_OK) {
     long long nelem = 1;
     double jac = 1.0;

@@ -339,9 +339,11 @@ int ndg_partition_set_state(ndg_partition* P, const void* src, size_t nbytes, in
   if (e != cudaSuccess) return cuda_fail(e, "state copy");
   int rc = copy_parts(P, true);
   if (rc) return rc;
-  e = cudaStreamSynchronize(P->stream);
+  // a new state: flags raised by earlier steps no longer apply
+  for (ndg_ctx* c : P->ctx) ndg_ctx_mark_state(c, P->stream);
+  e = cudaMemsetAsync(&P->group.d_hdr->err, 0, sizeof(int), P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
   if (e != cudaSuccess) return cuda_fail(e, "state copy");
-  for (ndg_ctx* c : P->ctx) ndg_ctx_mark_state(c);
   P->have_state = true;
   P->t = 0.0;
   P->steps = 0;

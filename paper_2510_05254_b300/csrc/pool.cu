@@ -54,6 +54,8 @@ struct PoolSolve {
   size_t need = 0;  // device bytes while admitted
   std::vector<char> host;  // initial state, then the result
   void* buf[kNumRoles] = {nullptr};
+  int* d_status = nullptr;  // set by a stage kernel whose bulk-copy wait ran out (SolveDesc::status)
+  int h_status = 0;         // its value, read back when the solve retires
   SolveDesc desc{};
   SolveState state = kQueued;
   cudaEvent_t ev = nullptr;  // upload done / last step done
@@ -94,7 +96,6 @@ struct ndg_pool {
   std::string worker_error;
   // batching state (worker thread only)
   std::map<long long, PoolClass> classes;
-  unsigned long long steps_checked = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_dirty = true;
   std::deque<cudaEvent_t> inflight;  // events of launched steps (bounded look-ahead)
@@ -295,13 +296,6 @@ void worker_main(ndg_pool* p) {
       cudaEventSynchronize(p->inflight.front());
       cudaEventDestroy(p->inflight.front());
       p->inflight.pop_front();
-      // every 32 steps: did a stage kernel flag a bulk-copy wait that ran out?
-      if ((++p->steps_checked & 31) == 0)
-        for (auto& kv : p->classes)
-          if (group_check(kv.second.group) != NDG_OK) {
-            std::lock_guard<std::mutex> lk(p->mu);
-            p->worker_error = ndg_last_error();
-          }
     }
   }
   while (!p->inflight.empty()) {
@@ -336,9 +330,12 @@ void io_main(ndg_pool* p) {
       const int roles = num_roles_for(s->rk);
       cudaError_t e = cudaSuccess;
       for (int r = 0; r < roles && e == cudaSuccess; ++r) e = cudaMallocAsync(&s->buf[r], s->state_bytes, p->io_stream);
+      if (e == cudaSuccess) e = cudaMallocAsync((void**)&s->d_status, 256, p->io_stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, sizeof(int), p->io_stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->buf[kUN], s->host.data(), s->state_bytes, cudaMemcpyHostToDevice, p->io_stream);
       for (int r = 0; r < kNumRoles; ++r) s->desc.buf[r] = s->buf[r];
+      s->desc.status = s->d_status;
       if (e == cudaSuccess) e = cudaEventRecord(s->ev, p->io_stream);
       std::lock_guard<std::mutex> lk(p->mu);
       if (e != cudaSuccess) {
@@ -355,12 +352,18 @@ void io_main(ndg_pool* p) {
       cudaStreamWaitEvent(p->io_stream, s->ev, 0);
       cudaError_t e = cudaMemcpyAsync(s->host.data(), s->buf[kUN], s->state_bytes, cudaMemcpyDeviceToHost,
                                       p->io_stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&s->h_status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->io_stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(p->io_stream);
       for (int r = 0; r < kNumRoles; ++r)
         if (s->buf[r]) {
           cudaFreeAsync(s->buf[r], p->io_stream);
           s->buf[r] = nullptr;
         }
+      if (s->d_status) {
+        cudaFreeAsync(s->d_status, p->io_stream);
+        s->d_status = nullptr;
+      }
       std::lock_guard<std::mutex> lk(p->mu);
       if (e != cudaSuccess) p->worker_error = cudaGetErrorString(e);
       s->state = kDone;
@@ -493,7 +496,11 @@ int ndg_pool_poll(ndg_pool* p, uint64_t ticket, void* result, size_t nbytes, ndg
     stats->device_bytes = s->need;
   }
   if (s->ev) cudaEventDestroy(s->ev);
+  const int st = s->h_status;
   p->solves.erase(it);
+  if (st == kStageErrBulkWait)
+    return fail(NDG_ECUDA, "solve %llu: a stage kernel's bulk copy into shared memory did not complete within "
+                "the wait limit (the result is not valid)", (unsigned long long)ticket);
   if (!p->worker_error.empty()) {
     std::string m = p->worker_error;
     return fail(NDG_ECUDA, "pool worker: %s", m.c_str());
@@ -543,6 +550,7 @@ int ndg_pool_destroy(ndg_pool* p) {
     PoolSolve* s = kv.second.get();
     for (int r = 0; r < kNumRoles; ++r)
       if (s->buf[r]) cudaFreeAsync(s->buf[r], p->io_stream);
+    if (s->d_status) cudaFreeAsync(s->d_status, p->io_stream);
     if (s->ev) cudaEventDestroy(s->ev);
   }
   cudaStreamSynchronize(p->io_stream);

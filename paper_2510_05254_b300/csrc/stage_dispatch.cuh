@@ -46,6 +46,27 @@ const BasisFF& basis_ff(int N) {
   return table[N];
 }
 
+const BasisPairs& basis_pairs(int N) {
+  static BasisPairs table[kMaxDegree + 1];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int d = 1; d <= kMaxDegree; ++d) {
+      Basis b;
+      build_basis(d, &b);
+      BasisPairs& t = table[d];
+      std::memset(&t, 0, sizeof(t));
+      const int n = d + 1, h = n / 2;
+      for (int i = 0; i < h; ++i)
+        for (int m = 0; m < h; ++m) {
+          const float ae = (float)b.Ae[i * kMaxN + m], bo = (float)b.Bo[i * kMaxN + m];
+          t.Ae[i * 4 + m] = make_float2(ae, ae);
+          t.Bo[i * 4 + m] = make_float2(bo, bo);
+        }
+    }
+  });
+  return table[N];
+}
+
 template <typename real>
 const BasisArgs<real>& basis_args(int N) {
   static BasisArgs<real> table[kMaxDegree + 1];
@@ -79,8 +100,8 @@ const BasisArgs<real>& basis_args(int N) {
 // picks one per kernel class.
 template <int N, int EQ>
 void shape_of(int variant, int epb, int* threads, size_t* smem) {
-  if (variant == kLineVarKernel) stage_shape<NDG_DIM, N, EQ, NDG_REAL, true>(epb, threads, smem);
-  else stage_shape<NDG_DIM, N, EQ, NDG_REAL, false>(epb, threads, smem);
+  if (variant == kLineVarKernel) stage_shape<NDG_DIM, N, EQ, NDG_REAL, true, NDG_FF, NDG_EXACT>(epb, threads, smem);
+  else stage_shape<NDG_DIM, N, EQ, NDG_REAL, false, NDG_FF, NDG_EXACT>(epb, threads, smem);
 }
 
 template <int N, int EQ, bool VS>
@@ -97,6 +118,7 @@ int launch_one(int variant, int grid, int epb, const SolveDesc* solves, const Gr
   args.plan = plan;
   args.basis = basis_args<NDG_REAL>(N);
   args.bff = basis_ff(N);
+  args.bp = basis_pairs(N);
   int threads;
   size_t smem;
   shape_of<N, EQ>(variant, epb, &threads, &smem);

@@ -54,13 +54,21 @@ struct BasisArgs {
   real Lhi[8];   // exact mass: w_N (M^-1 e_N)_l
 };
 
+// The even-odd halves in FP32 with every coefficient twice, (c, c): operands of the paired FP32
+// instructions (FFMA2 / FMUL2) that apply one coefficient to two variables at once.
+struct BasisPairs {
+  float2 Ae[16];
+  float2 Bo[16];
+};
+
 template <typename real>
 struct StageArgs {
   const SolveDesc* solves;
   const GroupHeader* hdr;
   StagePlan plan;
   BasisArgs<real> basis;
-  BasisFF bff;  // float-float halves of the same tables (FP64 path with float-float contraction)
+  BasisFF bff;     // float-float halves of the same tables (FP64 path with float-float contraction)
+  BasisPairs bp;   // paired FP32 halves (FP32 3D isothermal Euler at degrees 5 and 7)
 };
 
 // Per-solve coefficients in the kernel's precision (no conversion in device code).
@@ -159,9 +167,9 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 // Bulk (TMA) copies of contiguous global blocks into shared memory, completed on an mbarrier
 // that counts the bytes: one thread arms the barrier with the total and issues the copies, every
-// thread waits for the phase.  The wait is bounded: it gives up after kBulkWaitTries polls (each
-// of which may suspend the thread for a while), and the caller then reports the failure.
-constexpr int kBulkWaitTries = 1 << 22;
+// thread waits for the phase.  The wait is bounded: it gives up after a number of polls (each of
+// which may suspend the thread for a while; kBulkWaitPolls unless the launch's header sets
+// another), and the caller then reports the failure.
 __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(s) : "memory");
@@ -181,9 +189,9 @@ __device__ __forceinline__ void bulk_copy(void* smem_dst, const void* gmem_src, 
                : "memory");
 }
 // true once the barrier's phase of the given parity has completed; false if the polls ran out
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int polls) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(bar);
-  for (int i = 0; i < kBulkWaitTries; ++i) {
+  for (int i = 0; i < polls; ++i) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -434,6 +442,17 @@ __device__ __forceinline__ void contract_line(const real (&f)[N + 1], real (&out
   contract_even_odd<N>(f, out, args.basis);
 }
 
+// A bulk-copy wait ran out: flag the launch and every solve in it (the CTA that gives up leaves
+// tiles of any of them unprocessed), for the host to report.  Called by one thread.
+template <typename real>
+__device__ __noinline__ void flag_failure(const StageArgs<real>& args) {
+  GroupHeader* h = const_cast<GroupHeader*>(args.hdr);
+  atomicExch(&h->err, kStageErrBulkWait);
+  const int ns = h->nsolves;
+  for (int i = 0; i < ns; ++i)
+    if (args.solves[i].status) atomicExch(args.solves[i].status, kStageErrBulkWait);
+}
+
 template <int DIM, int N, int EQ, typename real, bool VS = false>
 struct StageGeom {
   static constexpr int n = N + 1;
@@ -518,17 +537,18 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const GroupHeader hdr = *args.hdr;
   const int epb = hdr.epb;
-  real* sU = reinterpret_cast<real*>(smem_raw);  // [NV][epb][SPE]
-  real* sR = sU + NV * epb * SPE;                 // [NV][epb][SPE]
-  real* sV = sR + NV * epb * SPE;                 // [DIM][epb][SPE] (Euler)
-  real* sB = sU + G::NS * epb * SPE;              // [NV][epb][NPE]: U^n of the tile (stage update)
-  real* sA = sB + NV * epb * NPE;                 // [NV][epb][NPE]: ACC of the tile
+  real* const sU = reinterpret_cast<real*>(smem_raw);  // [NV][epb][SPE]: the stage-input tile
+  real* sR = sU + NV * epb * SPE;                       // [NV][epb][SPE]
+  real* sV = sR + NV * epb * SPE;                       // [DIM][epb][SPE] (Euler)
+  real* sB = sU + G::NS * epb * SPE;                    // [NV][epb][NPE]: U^n of the tile (stage update)
+  real* sA = sB + NV * epb * NPE;                       // [NV][epb][NPE]: ACC of the tile
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
   const StagePlan& plan = args.plan;
   // BULK: the mbarrier of the tile copies, after the arrays (16-byte aligned)
   unsigned long long* const mbar = reinterpret_cast<unsigned long long*>(
       smem_raw + (((size_t)G::NS * SPE + (size_t)G::NB * NPE) * epb * sizeof(real) + 15) / 16 * 16);
+  const int polls = hdr.wait_polls > 0 ? hdr.wait_polls : kBulkWaitPolls;
   if constexpr (G::BULK) {
     if (tid == 0) mbar_init(mbar);
     __syncthreads();
@@ -678,37 +698,41 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
         fence_proxy_async_smem();
         const unsigned bytes = (unsigned)(cnt * NPE * sizeof(real));  // 864 / 2048-byte elements
         if (tid == 0) mbar_expect_tx(mbar, bytes * NV);
-        if constexpr (G::PLANE) {
-          // one copy per plane, spread over the first warp (after the expected byte count is set)
-          __syncwarp();
-          constexpr unsigned kPlane = n * n * sizeof(real);
-          const int planes = cnt * n;
-          for (int k = tid; k < NV * planes; k += 32) {
-            const int v = k / planes, pl = k - v * planes;
-            const int el = pl / n, z = pl - el * n;
-            bulk_copy(sU + (v * epb + el) * SPE + z * G::PS, uin + v * vstride + e0 * NPE + pl * (n * n), kPlane,
-                      mbar);
-          }
-        } else if (tid == 0) {
+        if (!hdr.stall_copies) {
+          if constexpr (G::PLANE) {
+            // one copy per plane, spread over the first warp (after the expected byte count is set)
+            __syncwarp();
+            constexpr unsigned kPlane = n * n * sizeof(real);
+            const int planes = cnt * n;
+            for (int k = tid; k < NV * planes; k += 32) {
+              const int v = k / planes, pl = k - v * planes;
+              const int el = pl / n, z = pl - el * n;
+              bulk_copy(sU + (v * epb + el) * SPE + z * G::PS, uin + v * vstride + e0 * NPE + pl * (n * n), kPlane,
+                        mbar);
+            }
+          } else if (tid == 0) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) bulk_copy(sU + v * epb * SPE, uin + v * vstride + e0 * NPE, bytes, mbar);
+            for (int v = 0; v < NV; ++v) bulk_copy(sU + v * epb * SPE, uin + v * vstride + e0 * NPE, bytes, mbar);
+          }
         }
         if constexpr (BPF) {
           if (tid == 0) prefetch_update_operands();
         }
       }
-      const bool ok = mbar_wait(mbar, bulk_phase);
+      const bool ok = mbar_wait(mbar, bulk_phase, polls);
       if (!__syncthreads_and(ok)) {
-        // the copies did not land in time: flag the group for the host, give the copies in flight
-        // one more bounded wait, and leave
-        if (tid == 0) atomicExch(&const_cast<GroupHeader*>(args.hdr)->err, kStageErrBulkWait);
-        mbar_wait(mbar, bulk_phase);
+        // the copies did not land in time: flag the launch for the host, give the copies in
+        // flight one more bounded wait, and leave
+        if (tid == 0) flag_failure(args);
+        mbar_wait(mbar, bulk_phase, polls);
         return;
       }
       bulk_phase ^= 1u;
     }
-    cp_async_wait_all();
-    __syncthreads();
+    if constexpr (!G::BULK) {  // (BULK: the vote on the wait above was the barrier)
+      cp_async_wait_all();
+      __syncthreads();
+    }
     // ---- 2. velocities (Euler; the FP32 kernel recomputes them per line instead) ----
     if constexpr (EQ == 1 && !G::SLIM) {
       const int total = cnt * NPE;
@@ -1017,9 +1041,24 @@ __global__ void stage_kernel(const StageArgs<real> args) {
 // The same with the register budget capped at 96 per thread (no spills), used for FP32 3D: one CTA
 // per SM more than the compiler's own choice of 106 allows (FP32 3D Euler 1.34 -> 1.24 ms per
 // stage).  A cap on the other classes would not be neutral: it changes the compiler's allocation.
+}  // namespace ndg
+
+#include "stage_euler3d_f32.cuh"
+
+namespace ndg {
+
+// The classes served by euler3d_f32_body: FP32 isothermal Euler in 3D at degrees 5 and 7, one
+// thread per line, lumped mass (the line-and-variable mapping and the exact-mass variant stay on
+// stage_body).
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF, bool EXACT>
+constexpr bool use_euler3d_f32() {
+  return DIM == 3 && sizeof(real) == 4 && EQ == 1 && (N == 5 || N == 7) && !VS && !FF && !EXACT;
+}
+
 template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 __global__ void __maxnreg__(96) stage_kernel_r96(const StageArgs<real> args) {
-  stage_body<DIM, N, EQ, real, VS, FF, EXACT>(args);
+  if constexpr (use_euler3d_f32<DIM, N, EQ, real, VS, FF, EXACT>()) euler3d_f32_body<N>(args);
+  else stage_body<DIM, N, EQ, real, VS, FF, EXACT>(args);
 }
 // The entry point of a kernel class.
 template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
@@ -1028,10 +1067,14 @@ constexpr auto stage_entry() {
   else return &stage_kernel<DIM, N, EQ, real, VS, FF, EXACT>;
 }
 
-template <int DIM, int N, int EQ, typename real, bool VS>
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 void stage_shape(int epb, int* threads, size_t* smem) {
   using G = StageGeom<DIM, N, EQ, real, VS>;
   *threads = epb * G::TPE;
+  if constexpr (use_euler3d_f32<DIM, N, EQ, real, VS, FF, EXACT>()) {
+    *smem = euler3d_f32_smem<N>(epb);
+    return;
+  }
   *smem = ((size_t)G::NS * G::SPE + (size_t)G::NB * G::NPE) * epb * sizeof(real);
   if constexpr (G::BULK) *smem = (*smem + 15) / 16 * 16 + 16;  // + the bulk copies' mbarrier
 }

@@ -75,6 +75,7 @@ _SIGS = {
     "ndg_norms": [_P, _P, ctypes.c_int, ctypes.POINTER(ndg_norms_t)],
     "ndg_stable_dt": [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     "ndg_norms_noalloc": [ctypes.POINTER(ndg_config), _P, _P, ctypes.c_int, _P, _P],
+    "ndg_debug_stall_copies": [ctypes.c_int],
     "ndg_node_coords": [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t],
     "ndg_info": [_P, ctypes.POINTER(ndg_info_t)],
     "ndg_lgl": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -224,6 +225,12 @@ def ndg_stream(ctx) -> int:
 
 def ndg_synchronize(ctx) -> None:
     _call("ndg_synchronize", ctx)
+
+
+def ndg_debug_stall_copies(polls: int) -> None:
+    """Test hook: work lists uploaded from now on make bulk-copy waits run out after `polls`
+    polls (0 restores normal operation)."""
+    _call("ndg_debug_stall_copies", int(polls))
 
 
 _alloc_keep = []

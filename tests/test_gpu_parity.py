@@ -407,16 +407,19 @@ def test_both_kernel_mappings(kernel, dim, N, E, eq):
         s = Solver(dim, N, E, elems_per_block=2, kernel=kernel, **kw)
         assert s.kernel == kernel
         check(p, s, U, dt, 2, rk, F64_TOL)
-    for dtype in ("f64", "f32"):
-        outs = []
-        for kern in (nat.NDG_KERNEL_LINE, nat.NDG_KERNEL_LINE_VAR):
-            s = Solver(dim, N, E, elems_per_block=2, kernel=kern, dtype=dtype, **kw)
-            s.set_state(U)
-            s.step(dt, 2, 4)
-            outs.append(s.get_state())
-        assert np.array_equal(outs[0], outs[1])
-    ref = orc.step(p, U.astype(np.float32).astype(np.float64), dt, 2, 4)
-    assert rel_l2(outs[1], ref) < 2 * F32_TOL
+    # FP32 with every scheme: the stage plans with ACC accumulation (RK3) and stored slopes (RK6)
+    for dtype, rks in (("f64", (4,)), ("f32", (3, 4, 6))):
+        for rk in rks:
+            outs = []
+            for kern in (nat.NDG_KERNEL_LINE, nat.NDG_KERNEL_LINE_VAR):
+                s = Solver(dim, N, E, elems_per_block=2, kernel=kern, dtype=dtype, **kw)
+                s.set_state(U)
+                s.step(dt, 2, rk)
+                outs.append(s.get_state())
+            assert np.array_equal(outs[0], outs[1]), (dtype, rk)
+            if dtype == "f32" and rk == 4:
+                ref = orc.step(p, U.astype(np.float32).astype(np.float64), dt, 2, 4)
+                assert rel_l2(outs[1], ref) < 2 * F32_TOL
 
 
 # ---- FP64 state with the float-float contraction (NDG_F64_FF): the FP64 parity bar ----

@@ -98,3 +98,30 @@ def test_unpadded_degree5_layout_fp32_2d():
     padded = dict(RS=n + 1, PS=(n + 1) * n, SPE=(n + 1) * n)
     assert line_access_ways(2, n, a=0, width=2, **dense) == 1  # x-lines as float2
     assert line_access_ways(2, n, a=1, width=1, **dense) <= line_access_ways(2, n, a=1, width=1, **padded)
+
+
+E3F_HEADER = os.path.join(os.path.dirname(HEADER), "stage_euler3d_f32.cuh")
+
+
+def test_element_major_layouts_fp32_3d_euler():
+    """euler3d_f32_body keeps each element's four variables together ([element][variable][SPE]);
+    the element stride ES sets the banks of a warp whose lines straddle two elements."""
+    h = open(E3F_HEADER).read()
+    assert "static constexpr int ES = NV * SPE + (PLANE ? 0 : 24);" in h
+    assert "static constexpr int PS = PLANE ? n * n + 8 : n * n;" in h
+    # degree 5: ES = 4 * 216 + 24 = 888 words (= 24 mod 32, as the variable-major 216)
+    n, ES = 6, 4 * 216 + 24
+    ways = [line_access_ways(3, n, n, n * n, ES, a, 2 if a == 0 else 1, nwarps=9) for a in range(3)]
+    old = [line_access_ways(3, n, n, n * n, 216, a, 2 if a == 0 else 1, nwarps=9) for a in range(3)]
+    assert ways == old == [1, 2, 2]
+    # the padding that was not chosen: 8 words would make the y-lines 4-way
+    assert line_access_ways(3, n, n, n * n, 4 * 216 + 8, 1, 1, nwarps=9) == 4
+    # the update's quads: a quarter-warp's eight float4 reads are conflict-free across elements
+    for q0 in range(0, 4 * 54, 8):
+        words = [divmod(q, 54)[0] * ES + 4 * divmod(q, 54)[1] for q in range(q0, q0 + 8)]
+        assert wavefronts(words * 4, 4) == 1
+    assert (ES * 4) % 16 == 0 and (216 * 4) % 16 == 0  # bulk-copy destinations 16-byte aligned
+    # degree 7: ES = 4 * 576; a warp never leaves its element, so the plane layout's analysis holds
+    n, PS = 8, 72
+    ES = 4 * n * PS
+    assert [line_access_ways(3, n, n, PS, ES, a, 4 if a == 0 else 1, nwarps=8) for a in range(3)] == [2, 1, 1]
