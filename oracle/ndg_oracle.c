@@ -47,9 +47,10 @@
  * Layout (the interface shared with the library, so that one array feeds both):
  *   U[v][e][node], v < nvar, e = ex + Ex*(ey + Ey*ez), node = i + n*(j + n*k).
  *
- * Build: gcc -O2 -std=c99 -ffp-contract=off -fPIC -shared ndg_oracle.c -lm
+ * Build: gcc -O2 -std=c99 -ffp-contract=off -pthread -fPIC -shared ndg_oracle.c -lm
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -321,7 +322,9 @@ static void numerical_flux(const orc_problem* p, int axis, const double* uL, con
 /* Spatial operator R = L(U)                                                                    */
 /* ------------------------------------------------------------------------------------------ */
 
-int orc_rhs(const orc_problem* p, const double* U, double* R) {
+/* R = L(U) on the elements [e_begin, e_end) only (their nodes of every variable); U is read on
+ * those elements and their face neighbours.  orc_rhs is the whole range. */
+static int rhs_elements(const orc_problem* p, const double* U, double* R, int64_t e_begin, int64_t e_end) {
   if (check_problem(p)) return -1;
   int N = p->degree, n = N + 1, d = p->dim, nv = nvar_of(p);
   double xi[ORC_MAXN], w[ORC_MAXN], D[ORC_MAXN * ORC_MAXN];
@@ -339,10 +342,12 @@ int orc_rhs(const orc_problem* p, const double* U, double* R) {
   int64_t ne = (int64_t)E[0] * E[1] * E[2];
   int64_t nd = ne * np * nv;
   int stride[3] = {1, n, n * n}; /* node-index stride along each axis */
-  for (int64_t q = 0; q < nd; ++q) R[q] = 0.0;
+  (void)nd;
+  for (int v = 0; v < nv; ++v)
+    for (int64_t q = ((int64_t)v * ne + e_begin) * np; q < ((int64_t)v * ne + e_end) * np; ++q) R[q] = 0.0;
 
   double u[ORC_MAXN][4], F[ORC_MAXN][4], uLn[4], uRn[4], fhatL[4], fhatR[4], b[ORC_MAXN][4];
-  for (int64_t e = 0; e < ne; ++e) {
+  for (int64_t e = e_begin; e < e_end; ++e) {
     int ei[3] = {(int)(e % E[0]), (int)((e / E[0]) % E[1]), (int)(e / ((int64_t)E[0] * E[1]))};
     for (int a = 0; a < d; ++a) {
       double h = p->length[a] / E[a];
@@ -395,16 +400,42 @@ int orc_rhs(const orc_problem* p, const double* U, double* R) {
   return 0;
 }
 
+int orc_rhs(const orc_problem* p, const double* U, double* R) {
+  if (check_problem(p)) return -1;
+  int64_t ne = 1;
+  for (int a = 0; a < p->dim; ++a) ne *= p->elems[a];
+  return rhs_elements(p, U, R, 0, ne);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Runge-Kutta schemes of Sec. 2.3, generic over the right-hand side                            */
 /* ------------------------------------------------------------------------------------------ */
 
-typedef int (*rhs_fn)(const void* ctx, const double* U, double* R);
+/* The part of the unknowns one caller updates: index spans [lo, hi), the element range its
+ * right-hand side covers, and a barrier that every caller passes before and after each
+ * right-hand-side evaluation (NULL for a single caller).  One caller owning everything is the
+ * plain sequential scheme; several callers with disjoint parts (orc_step_threads) perform the
+ * same operations on every unknown, so their result is bitwise the sequential one. */
+typedef struct {
+  const int64_t* lo;
+  const int64_t* hi;
+  int nspans;
+  int64_t e_begin, e_end;
+  void (*sync)(void* ctx);
+  void* sync_ctx;
+} orc_part;
 
-/* One step of size dt of the scheme `rk` (3, 4 or 6) for U' = F(U), n unknowns.
- * work must hold 9 * n doubles. */
+typedef int (*rhs_fn)(const void* ctx, const double* U, double* R, const orc_part* part);
+
+#define OWN(i) for (int s_ = 0; s_ < part->nspans; ++s_) for (i = part->lo[s_]; i < part->hi[s_]; ++i)
+#define SYNC() do { if (part->sync) part->sync(part->sync_ctx); } while (0)
+/* F evaluated once every caller has written its stage argument, and before any overwrites it */
+#define EVAL(Y) do { SYNC(); if (F(ctx, (Y), Fy, part)) return -1; SYNC(); } while (0)
+
+/* One step of size dt of the scheme `rk` (3, 4 or 6) for U' = F(U) on this caller's part of
+ * the n unknowns.  work must hold 9 * n doubles (shared by all callers). */
 static int rk_advance(int rk, int64_t n, double* U, double dt, rhs_fn F, const void* ctx,
-                      double* work) {
+                      double* work, const orc_part* part) {
   double* k1 = work;
   double* k2 = work + n;
   double* k3 = work + 2 * n;
@@ -416,71 +447,71 @@ static int rk_advance(int rk, int64_t n, double* U, double dt, rhs_fn F, const v
   double* Fy = work + 8 * n; /* F(Y) */
   int64_t i;
   if (rk == 3) { /* Eq. (RK3), reading 5 */
-    if (F(ctx, U, Fy)) return -1;
-    for (i = 0; i < n; ++i) k1[i] = dt * Fy[i] / 3.0;
-    for (i = 0; i < n; ++i) Y[i] = U[i] + k1[i];
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k2[i] = 2.0 * dt * Fy[i] / 3.0;
-    for (i = 0; i < n; ++i) Y[i] = U[i] + k2[i];
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k3[i] = (3.0 * k1[i] + 3.0 * dt * Fy[i]) / 4.0;
-    for (i = 0; i < n; ++i) U[i] = U[i] + k3[i];
+    EVAL(U);
+    OWN(i) k1[i] = dt * Fy[i] / 3.0;
+    OWN(i) Y[i] = U[i] + k1[i];
+    EVAL(Y);
+    OWN(i) k2[i] = 2.0 * dt * Fy[i] / 3.0;
+    OWN(i) Y[i] = U[i] + k2[i];
+    EVAL(Y);
+    OWN(i) k3[i] = (3.0 * k1[i] + 3.0 * dt * Fy[i]) / 4.0;
+    OWN(i) U[i] = U[i] + k3[i];
     return 0;
   }
   if (rk == 4) { /* Eq. (RK4) */
-    if (F(ctx, U, Fy)) return -1;
-    for (i = 0; i < n; ++i) k1[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i) Y[i] = U[i] + k1[i] / 2.0;
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k2[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i) Y[i] = U[i] + k2[i] / 2.0;
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k3[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i) Y[i] = U[i] + k3[i];
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k4[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i) U[i] = U[i] + (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]) / 6.0;
+    EVAL(U);
+    OWN(i) k1[i] = dt * Fy[i];
+    OWN(i) Y[i] = U[i] + k1[i] / 2.0;
+    EVAL(Y);
+    OWN(i) k2[i] = dt * Fy[i];
+    OWN(i) Y[i] = U[i] + k2[i] / 2.0;
+    EVAL(Y);
+    OWN(i) k3[i] = dt * Fy[i];
+    OWN(i) Y[i] = U[i] + k3[i];
+    EVAL(Y);
+    OWN(i) k4[i] = dt * Fy[i];
+    OWN(i) U[i] = U[i] + (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]) / 6.0;
     return 0;
   }
   if (rk == 6) { /* Eq. (RK6), Luther's seven-stage sixth-order scheme, as printed */
     const double s = sqrt(21.0);
-    if (F(ctx, U, Fy)) return -1;
-    for (i = 0; i < n; ++i) k1[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i) Y[i] = U[i] + k1[i];
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k2[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i) Y[i] = U[i] + (3.0 * k1[i] + k2[i]) / 8.0;
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k3[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i) Y[i] = U[i] + (8.0 * k1[i] + 2.0 * k2[i] + 8.0 * k3[i]) / 27.0;
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k4[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i)
+    EVAL(U);
+    OWN(i) k1[i] = dt * Fy[i];
+    OWN(i) Y[i] = U[i] + k1[i];
+    EVAL(Y);
+    OWN(i) k2[i] = dt * Fy[i];
+    OWN(i) Y[i] = U[i] + (3.0 * k1[i] + k2[i]) / 8.0;
+    EVAL(Y);
+    OWN(i) k3[i] = dt * Fy[i];
+    OWN(i) Y[i] = U[i] + (8.0 * k1[i] + 2.0 * k2[i] + 8.0 * k3[i]) / 27.0;
+    EVAL(Y);
+    OWN(i) k4[i] = dt * Fy[i];
+    OWN(i)
       Y[i] = U[i] + (3.0 * (3.0 * s - 7.0) * k1[i] - 8.0 * (7.0 - s) * k2[i] +
                      48.0 * (7.0 - s) * k3[i] - 3.0 * (21.0 - s) * k4[i]) / 392.0;
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k5[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i)
+    EVAL(Y);
+    OWN(i) k5[i] = dt * Fy[i];
+    OWN(i)
       Y[i] = U[i] + (-5.0 * (231.0 + 51.0 * s) * k1[i] - 40.0 * (7.0 + s) * k2[i] -
                      320.0 * s * k3[i] + 3.0 * (21.0 + 121.0 * s) * k4[i] +
                      392.0 * (6.0 + s) * k5[i]) / 1960.0;
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k6[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i)
+    EVAL(Y);
+    OWN(i) k6[i] = dt * Fy[i];
+    OWN(i)
       Y[i] = U[i] + (15.0 * (22.0 + 7.0 * s) * k1[i] + 120.0 * k2[i] +
                      40.0 * (7.0 * s - 5.0) * k3[i] - 63.0 * (3.0 * s - 2.0) * k4[i] -
                      14.0 * (49.0 + 9.0 * s) * k5[i] + 70.0 * (7.0 - s) * k6[i]) / 180.0;
-    if (F(ctx, Y, Fy)) return -1;
-    for (i = 0; i < n; ++i) k7[i] = dt * Fy[i];
-    for (i = 0; i < n; ++i)
+    EVAL(Y);
+    OWN(i) k7[i] = dt * Fy[i];
+    OWN(i)
       U[i] = U[i] + (9.0 * k1[i] + 64.0 * k3[i] + 49.0 * k5[i] + 49.0 * k6[i] + 9.0 * k7[i]) / 180.0;
     return 0;
   }
   return -1;
 }
 
-static int pde_rhs(const void* ctx, const double* U, double* R) {
-  return orc_rhs((const orc_problem*)ctx, U, R);
+static int pde_rhs(const void* ctx, const double* U, double* R, const orc_part* part) {
+  return rhs_elements((const orc_problem*)ctx, U, R, part->e_begin, part->e_end);
 }
 
 /* nsteps steps of size dt of scheme rk (3, 4, 6) on the NDG semi-discretisation, in place. */
@@ -489,9 +520,128 @@ int orc_step(const orc_problem* p, double* U, double dt, int nsteps, int rk) {
   int64_t nd = orc_ndof(p);
   double* work = (double*)malloc(sizeof(double) * 9 * (size_t)nd);
   if (!work) return -2;
+  const int64_t lo = 0, hi = nd;
+  const orc_part whole = {&lo, &hi, 1, 0, nd / nvar_of(p) / ipow(p->degree + 1, p->dim), NULL, NULL};
   int rc = 0;
-  for (int s = 0; s < nsteps && rc == 0; ++s) rc = rk_advance(rk, nd, U, dt, pde_rhs, p, work);
+  for (int s = 0; s < nsteps && rc == 0; ++s) rc = rk_advance(rk, nd, U, dt, pde_rhs, p, work, &whole);
   free(work);
+  return rc;
+}
+
+/* ---- the same scheme split over threads, for timing on a multi-core host ---------------- */
+
+typedef struct {
+  pthread_mutex_t mu;
+  pthread_cond_t cv;
+  int count, total, generation;
+} orc_barrier;
+
+static void barrier_wait(void* ctx) {
+  orc_barrier* b = (orc_barrier*)ctx;
+  pthread_mutex_lock(&b->mu);
+  const int gen = b->generation;
+  if (++b->count == b->total) {
+    b->count = 0;
+    ++b->generation;
+    pthread_cond_broadcast(&b->cv);
+  } else {
+    while (gen == b->generation) pthread_cond_wait(&b->cv, &b->mu);
+  }
+  pthread_mutex_unlock(&b->mu);
+}
+
+typedef struct {
+  const orc_problem* p;
+  double* U;
+  double* work;
+  double dt;
+  int nsteps, rk, rc;
+  int64_t lo[4], hi[4];
+  orc_part part;
+} orc_worker;
+
+static void* worker_main(void* arg) {
+  orc_worker* w = (orc_worker*)arg;
+  const int64_t nd = orc_ndof(w->p);
+  w->rc = 0;
+  for (int s = 0; s < w->nsteps; ++s) {
+    /* every thread runs every step (a failing one still passes its barriers: its rc is kept) */
+    int rc = rk_advance(w->rk, nd, w->U, w->dt, pde_rhs, w->p, w->work, &w->part);
+    if (rc && !w->rc) w->rc = rc;
+  }
+  return NULL;
+}
+
+/* orc_step with the elements split into nthreads contiguous ranges, one thread each: every
+ * thread applies the scheme to the unknowns of its elements and evaluates the right-hand side
+ * there, with a barrier before and after each evaluation (the stage arguments of neighbouring
+ * elements are read across ranges).  Each unknown gets exactly the operations of orc_step, so
+ * the result is bitwise that of orc_step.  For timing only; the checker is orc_step. */
+int orc_step_threads(const orc_problem* p, double* U, double dt, int nsteps, int rk, int nthreads) {
+  if (check_problem(p) || nsteps < 0 || !(dt > 0.0) || (rk != 3 && rk != 4 && rk != 6)) return -1;
+  if (nthreads < 1 || nthreads > 4096) return -1;
+  const int64_t nd = orc_ndof(p), nv = nvar_of(p), np = ipow(p->degree + 1, p->dim);
+  const int64_t ne = nd / nv / np;
+  if (nthreads > ne) nthreads = (int)ne;
+  double* work = (double*)malloc(sizeof(double) * 9 * (size_t)nd);
+  orc_worker* ws = (orc_worker*)calloc((size_t)nthreads, sizeof(orc_worker));
+  pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+  if (!work || !ws || !th) {
+    free(work);
+    free(ws);
+    free(th);
+    return -2;
+  }
+  orc_barrier bar;
+  pthread_mutex_init(&bar.mu, NULL);
+  pthread_cond_init(&bar.cv, NULL);
+  bar.count = 0;
+  bar.total = nthreads;
+  bar.generation = 0;
+  for (int t = 0; t < nthreads; ++t) {
+    orc_worker* w = &ws[t];
+    const int64_t e0 = ne * t / nthreads, e1 = ne * (t + 1) / nthreads;
+    w->p = p, w->U = U, w->work = work, w->dt = dt, w->nsteps = nsteps, w->rk = rk;
+    for (int v = 0; v < nv; ++v) {
+      w->lo[v] = (v * ne + e0) * np;
+      w->hi[v] = (v * ne + e1) * np;
+    }
+    w->part.lo = w->lo, w->part.hi = w->hi, w->part.nspans = (int)nv;
+    w->part.e_begin = e0, w->part.e_end = e1;
+    w->part.sync = nthreads > 1 ? barrier_wait : NULL;
+    w->part.sync_ctx = &bar;
+  }
+  int started = 0, rc = 0;
+  for (int t = 1; t < nthreads; ++t) {
+    if (pthread_create(&th[t], NULL, worker_main, &ws[t]) != 0) {
+      rc = -3;
+      break;
+    }
+    ++started;
+  }
+  if (rc == 0) {
+    worker_main(&ws[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    for (int t = 0; t < nthreads && rc == 0; ++t) rc = ws[t].rc;
+  } else {
+    /* a thread could not start: the barrier counts the ones that did (and this one), they all
+     * run to the end (on a partial split, so the result is not used), then the call fails */
+    pthread_mutex_lock(&bar.mu);
+    bar.total = started + 1;
+    if (bar.count == bar.total) {
+      bar.count = 0;
+      ++bar.generation;
+      pthread_cond_broadcast(&bar.cv);
+    }
+    pthread_mutex_unlock(&bar.mu);
+    worker_main(&ws[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+  }
+  pthread_mutex_destroy(&bar.mu);
+  pthread_cond_destroy(&bar.cv);
+  free(work);
+  free(ws);
+  free(th);
   return rc;
 }
 
@@ -499,8 +649,9 @@ int orc_step(const orc_problem* p, double* U, double dt, int nsteps, int rk) {
  * which = 0: y' = lambda y;  which = 1: y' = -y^2. */
 typedef struct { int which; double lambda; } ode_ctx;
 
-static int ode_rhs(const void* ctx, const double* y, double* f) {
+static int ode_rhs(const void* ctx, const double* y, double* f, const orc_part* part) {
   const ode_ctx* c = (const ode_ctx*)ctx;
+  (void)part;
   f[0] = c->which == 0 ? c->lambda * y[0] : -y[0] * y[0];
   return 0;
 }
@@ -508,9 +659,11 @@ static int ode_rhs(const void* ctx, const double* y, double* f) {
 int orc_rk_ode(int rk, int which, double lambda, double y0, double dt, int nsteps, double* y) {
   double work[9];
   ode_ctx c = {which, lambda};
+  const int64_t lo = 0, hi = 1;
+  const orc_part one = {&lo, &hi, 1, 0, 1, NULL, NULL};
   y[0] = y0;
   for (int s = 0; s < nsteps; ++s)
-    if (rk_advance(rk, 1, y, dt, ode_rhs, &c, work)) return -1;
+    if (rk_advance(rk, 1, y, dt, ode_rhs, &c, work, &one)) return -1;
   return 0;
 }
 

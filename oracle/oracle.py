@@ -5,7 +5,9 @@ nodal DG + Runge-Kutta method of arXiv:2510.05254, Sec. 2.  Only the tests, the 
 the CPU-baseline leg of the benchmark use it; it imports nothing from the CUDA package, and the
 CUDA package never imports it.
 
-The shared library is built on first use with gcc (``-O2 -ffp-contract=off``), next to the source.
+The shared library is built on first use with gcc (``-O2 -ffp-contract=off``), next to the source;
+a second build of the same source with ``-O3 -march=native`` (per host CPU, under ``_build/``)
+serves the timed CPU baseline, alone or split over the host's cores (``step_threads``).
 """
 from __future__ import annotations
 
@@ -33,11 +35,39 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.run(
-            ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"],
+            ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-pthread", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"],
             check=True,
         )
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def _host_tag() -> str:
+    """A tag of this host's CPU (model and feature flags): a -march=native build is only valid on
+    the CPU it was compiled for."""
+    import hashlib
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = [l for l in f if l.startswith(("model name", "flags", "Features"))][:2]
+    except OSError:
+        info = [platform.processor()]
+    return hashlib.sha1("".join(info).encode()).hexdigest()[:12]
+
+
+def build_timing(force: bool = False) -> str:
+    """The same source for timing on this host: -O3 -march=native, still -ffp-contract=off (no
+    contraction; without -ffast-math the compiler may not reorder the sums either, so results are
+    bitwise those of the checking build -- tested).  Built per CPU under oracle/_build/."""
+    out_dir = os.path.join(_HERE, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, f"liboracle_native_{_host_tag()}.so")
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O3", "-march=native", "-std=c99", "-ffp-contract=off", "-pthread", "-fPIC",
+                        "-shared", _SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Problem(ctypes.Structure):
@@ -101,27 +131,42 @@ class Problem:
                         self.mass)
 
 
+def _declare(lib):
+    P = ctypes.POINTER(_Problem)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.orc_lgl.argtypes = [ctypes.c_int, dp, dp]
+    lib.orc_dmat.argtypes = [ctypes.c_int, dp, dp]
+    lib.orc_mass.argtypes = [ctypes.c_int, ctypes.c_int, dp]
+    lib.orc_rhs.argtypes = [P, dp, dp]
+    lib.orc_step.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    lib.orc_step_threads.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.orc_norms.argtypes = [P, dp, dp, dp]
+    lib.orc_stable_dt.argtypes = [P, dp, ctypes.c_double]
+    lib.orc_stable_dt.restype = ctypes.c_double
+    lib.orc_node_coords.argtypes = [P, dp]
+    lib.orc_ndof.argtypes = [P]
+    lib.orc_ndof.restype = ctypes.c_int64
+    lib.orc_rk_ode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_int, dp]
+    return lib
+
+
+_timing_lib = None
+
+
+def _load_timing():
+    global _timing_lib
+    with _lock:
+        if _timing_lib is None:
+            _timing_lib = _declare(ctypes.CDLL(build_timing()))
+    return _timing_lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.POINTER(_Problem)
-            dp = ctypes.POINTER(ctypes.c_double)
-            lib.orc_lgl.argtypes = [ctypes.c_int, dp, dp]
-            lib.orc_dmat.argtypes = [ctypes.c_int, dp, dp]
-            lib.orc_mass.argtypes = [ctypes.c_int, ctypes.c_int, dp]
-            lib.orc_rhs.argtypes = [P, dp, dp]
-            lib.orc_step.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
-            lib.orc_norms.argtypes = [P, dp, dp, dp]
-            lib.orc_stable_dt.argtypes = [P, dp, ctypes.c_double]
-            lib.orc_stable_dt.restype = ctypes.c_double
-            lib.orc_node_coords.argtypes = [P, dp]
-            lib.orc_ndof.argtypes = [P]
-            lib.orc_ndof.restype = ctypes.c_int64
-            lib.orc_rk_ode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                       ctypes.c_double, ctypes.c_int, dp]
-            _lib = lib
+            _lib = _declare(ctypes.CDLL(build()))
     return _lib
 
 
@@ -182,6 +227,31 @@ def step(p: Problem, U, dt: float, nsteps: int, rk: int = 4) -> np.ndarray:
     U = _f64(U).reshape(p.shape).copy()
     c = p._c()
     rc = _load().orc_step(ctypes.byref(c), _ptr(U), float(dt), int(nsteps), int(rk))
+    if rc != 0:
+        raise ValueError(f"orc_step failed ({rc})")
+    return U
+
+
+def step_threads(p: Problem, U, dt: float, nsteps: int, rk: int = 4, threads: int = 0,
+                 native: bool = False) -> np.ndarray:
+    """The same steps split over `threads` threads by element ranges (0: every core of the host);
+    bitwise equal to step().  For timing the CPU on many cores -- the checker is step().  native:
+    use the -O3 -march=native build of the same source (build_timing)."""
+    U = _f64(U).reshape(p.shape).copy()
+    c = p._c()
+    lib = _load_timing() if native else _load()
+    n = threads or (os.cpu_count() or 1)
+    rc = lib.orc_step_threads(ctypes.byref(c), _ptr(U), float(dt), int(nsteps), int(rk), int(n))
+    if rc != 0:
+        raise ValueError(f"orc_step_threads failed ({rc})")
+    return U
+
+
+def step_native(p: Problem, U, dt: float, nsteps: int, rk: int = 4) -> np.ndarray:
+    """step() from the -O3 -march=native build (timing on this host)."""
+    U = _f64(U).reshape(p.shape).copy()
+    c = p._c()
+    rc = _load_timing().orc_step(ctypes.byref(c), _ptr(U), float(dt), int(nsteps), int(rk))
     if rc != 0:
         raise ValueError(f"orc_step failed ({rc})")
     return U
