@@ -1,19 +1,22 @@
 """Benchmark of the NDG + RK hot path on B300: DOF-updates per second per RK stage.
 
-Workload (one bench step): the 2D linear advection problem of the paper's Sec. 3 at degree 7,
-256 x 256 quadrilateral elements (8 x 8 LGL nodes each, 2048^2 = 4.19M DOF), velocity (1, 0.5),
-Gaussian pulse exp(-r^2/0.01) at the centre plus seeded low-mode Fourier noise (amplitude 1e-3),
-upwind flux, classical RK4 at CFL 0.1, 1000 time steps, followed by the norms reduction.  The
-state is reset from a device-resident copy of the initial condition and L2 is flushed at the start
-of every bench step.  FP64 is the headline; the FP32 variant and a mixed serving stream are
-reported beside it; the FP64 CPU oracle (single thread, as it stands) gives the CPU baseline.
+Headline workload (one bench step): the 3D isothermal Euler problem of the paper's Sec. 3.2 at
+degree 5 -- 64^3 hexahedral elements of 6^3 LGL nodes, 4 x 384^3 = 226.5M DOF, rho = 1 and a
+Taylor-Green velocity of amplitude 0.1, local Lax-Friedrichs flux, classical RK4 at CFL 0.1 --
+advanced 10 RK4 steps (40 launches of the fused stage kernel) from its initial state, followed by
+the norms reduction.  The state is reset from a device-resident copy at the start of every bench
+step; every array (1.8 GB in FP64) is far larger than the 126 MB L2.  FP64 is the headline, FP32
+is reported beside it.  The line also carries: the same workload end to end through the C ABI
+with host buffers (`e2e`), the oracle on the host's cores (`cpu_baseline`), a table of the other
+problems (2D advection 256^2 and 2D isothermal Euler 512^2 at degree 7, 3D isothermal Euler
+32^3 at degree 7, and this one), each timed for at least 2.5 s with board power sampled (energy
+per DOF-update), and the serving stream (pool versus one solve at a time, Poisson arrivals at
+multiples of the one-at-a-time FP64 capacity).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-serving]
-                    [--no-workloads] [--workload adv2d|euler2d|euler3d|euler3d7] [--variants f64,f32,f64ff]
-
-Beside the headline, the line carries a table of the isothermal Euler problems (2D 512^2 at
-degree 7, 3D 64^3 at degree 5, 3D 32^3 at degree 7): FP64 and FP32 ms per stage with their
-roofline fractions.
+                    [--no-workloads] [--no-cpu-baseline] [--serving-solves S] [--serving-sweep-solves S]
+                    [--serving-only] [--workload euler3d|adv2d|euler2d|euler3d7] [--elems E] [--epb T]
+                    [--variants f64,f32,f64ff]
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload ("replicas only":
 the solve is not partitioned across GPUs); value = total DOF-updates / max rank time.
@@ -27,7 +30,6 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -36,43 +38,37 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF-updates/s per RK stage (FP64 vs FP32); batched solves/s + p50/p99 latency"
-# The bench workload (default) and the other full-size problems, selectable with
-# --workload: (dim, degree, elements, equation, velocity, RK steps per bench step, description).
+# name: (dim, degree, elements, equation, velocity, RK4 steps per bench step, description)
 WORKLOADS = {
+    "euler3d": (3, 5, (64, 64, 64), 1, (0.0, 0.0, 0.0), 10,
+                "3D isothermal Euler, 64^3 elements, degree 5 (6^3 LGL nodes), 4 x 384^3 = 226.5M DOF, "
+                "Taylor-Green velocity amplitude 0.1, LLF flux, RK4 at CFL 0.1"),
     "adv2d": (2, 7, (256, 256), 0, (1.0, 0.5, 0.0), 1000,
-              "2D linear advection, 256x256 elements, degree 7 (8x8 LGL nodes), 4.19M DOF, RK4, 1000 steps"),
+              "2D linear advection, 256^2 elements, degree 7 (8^2 LGL nodes), 2048^2 = 4.19M DOF, "
+              "velocity (1, 0.5), upwind flux, RK4 at CFL 0.1"),
     "euler2d": (2, 7, (512, 512), 1, (0.0, 0.0, 0.0), 200,
-                "2D isothermal Euler, 512x512 elements, degree 7, 3 x 4096^2 = 50.3M DOF, RK4, 200 steps"),
-    "euler3d": (3, 5, (64, 64, 64), 1, (0.0, 0.0, 0.0), 50,
-                "3D isothermal Euler, 64^3 elements, degree 5, 4 x 384^3 = 226.5M DOF, RK4, 50 steps"),
+                "2D isothermal Euler, 512^2 elements, degree 7, 3 x 4096^2 = 50.3M DOF, LLF flux, RK4 at CFL 0.1"),
     # the eighth-order 3D case (degree 7) at the same size class
     "euler3d7": (3, 7, (32, 32, 32), 1, (0.0, 0.0, 0.0), 50,
-                 "3D isothermal Euler, 32^3 elements, degree 7 (8^3 LGL nodes), 4 x 256^3 = 67.1M DOF, RK4, 50 steps"),
+                 "3D isothermal Euler, 32^3 elements, degree 7 (8^3 LGL nodes), 4 x 256^3 = 67.1M DOF, "
+                 "LLF flux, RK4 at CFL 0.1"),
 }
-DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD = WORKLOADS["adv2d"]
+HEADLINE = "euler3d"
+DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD = WORKLOADS[HEADLINE]
 CFL, RK = 0.1, 4
 STAGES = 4
-L2_FLUSH_BYTES = 256 << 20
-
-
-def select_workload(name):
-    global DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD
-    DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD = WORKLOADS[name]
-
-# Algorithmic work of one RK4 stage per DOF:
-#   flops, 2D advection degree 7: sum-factorised strong-form volume term 2 axes x 8 FMA (32 flop)
-#          + per-axis scaling (3) + lifted face terms (1.5) + stage update (3.5 on average over the
-#          4 stages) = 40 flop; 2D isothermal Euler degree 7: 48; 3D isothermal Euler degree 5: 60;
-#          3D isothermal Euler degree 7: 72 (volume 3 axes x 8 FMA = 48 instead of 3 x 6 = 36);
-#   bytes: RK4 array passes per stage 3, 5, 5, 3 -> 4 on average x sizeof(real).
+PASSES_PER_STAGE = 4.0  # RK4 array passes per stage: 3, 5, 5, 3
+# Algorithmic FP64 work of one RK4 stage per DOF (sum-factorised strong-form volume term d axes x
+# n FMA, per-axis scaling, lifted face terms, stage update averaged over the four stages): 2D
+# advection degree 7: 40 flop; 2D isothermal Euler degree 7: 48; 3D isothermal Euler degree 5:
+# 60; degree 7: 72 (the volume term 3 axes x 8 FMA = 48 instead of 3 x 6 = 36).
 FLOPS_PER_DOF = {"adv2d": 40.0, "euler2d": 48.0, "euler3d": 60.0, "euler3d7": 72.0}
-# DRAM bytes per stage launch of the bench workload's kernels (mean of the four RK4 stages), from
-# one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum (command and per-stage values in
-# profiles/stage_kernel_2d_advection_deg7_256x256.md); to be captured again when the kernel changes.
-TRAFFIC_PER_LAUNCH = {("adv2d", "f64"): 91.95e6, ("adv2d", "f32"): 37.79e6}
-FLOPS_PER_DOF_STAGE = FLOPS_PER_DOF["adv2d"]
-PASSES_PER_STAGE = 4.0
-
+# DRAM bytes (read + write) per stage launch of the headline's kernels, mean of the four RK4
+# stages, from ncu captures of dram__bytes_read.sum + dram__bytes_write.sum at 48^3 elements
+# scaled to 64^3 by the DOF count (commands and per-stage values in
+# profiles/stage_kernel_euler3d_deg5_64cubed.md); to be captured again when a kernel changes.
+TRAFFIC_PER_LAUNCH = {("euler3d", "f64"): 7.3295e9, ("euler3d", "f32"): 3.5634e9}
+L2_BYTES = 126e6
 
 _T0 = time.perf_counter()
 
@@ -81,6 +77,11 @@ def log(msg):
     """Progress on stderr (the JSON line alone goes to stdout)."""
     sys.stderr.write(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}\n")
     sys.stderr.flush()
+
+
+def select_workload(name):
+    global DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD
+    DIM, DEGREE, ELEMS, EQ, VEL, NSTEPS, WORKLOAD = WORKLOADS[name]
 
 
 def load_peaks():
@@ -96,8 +97,16 @@ def fp64_peak_tflops(sm_mhz):
     return 148 * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons / board power sampled every 200 ms during a timed
+    region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -182,86 +191,141 @@ def max_over_ranks(pg, x, dev):
     return float(t.item())
 
 
-def data_description():
-    """What the synthetic initial state of the selected workload is."""
-    if EQ == 0:
+def data_description(eq=None, dim=None):
+    eq = EQ if eq is None else eq
+    dim = DIM if dim is None else dim
+    if eq == 0:
         return "synthetic (seeded Gaussian pulse + Fourier noise)"
-    if DIM == 2:
+    if dim == 2:
         return "synthetic (isothermal Euler: density 1 + 0.1 sin sin, seeded smooth shear velocity, Mach <= 0.3)"
     return "synthetic (isothermal Euler: density 1, Taylor-Green velocity of amplitude 0.1)"
 
 
-def initial_condition(X):
+def initial_condition(X, eq=None, dim=None):
     from paper_2510_05254_b300 import inputs
-    if EQ == 0:
+    eq = EQ if eq is None else eq
+    dim = DIM if dim is None else dim
+    if eq == 0:
         return inputs.gaussian_noise(X)
-    return inputs.euler_shear(X) if DIM == 2 else inputs.taylor_green(X)
+    return inputs.euler_shear(X) if dim == 2 else inputs.taylor_green(X)
 
 
-def oracle_sample(nsteps):
-    """The FP64 oracle as it stands (single thread) on the full workload for nsteps RK4 steps."""
+def ndof_of(dim, degree, elems, eq):
+    return (1 if eq == 0 else dim + 1) * int(np.prod(elems)) * (degree + 1) ** dim
+
+
+def config_block(world):
+    return {"workload": WORKLOAD, "elements": list(ELEMS), "degree": DEGREE, "dof": ndof_of(DIM, DEGREE, ELEMS, EQ),
+            "rk_steps_per_bench_step": NSTEPS, "rk_scheme": "RK4 (Eq. (RK4))", "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2: every state array exceeds the 126 MB L2 "
+                  f"({ndof_of(DIM, DEGREE, ELEMS, EQ) * 8 / 1e9:.2f} GB in FP64)"}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU: the oracle (test infrastructure) timed on the host's cores
+# ---------------------------------------------------------------------------------------------
+
+def _oracle_problem(elems):
     from oracle import oracle as orc
-    p = orc.Problem(dim=DIM, degree=DEGREE, elems=tuple(ELEMS) + (1,) * (3 - DIM), equation=EQ, flux=EQ,
-                    velocity=VEL)
+    return orc.Problem(dim=DIM, degree=DEGREE, elems=tuple(elems) + (1,) * (3 - DIM), equation=EQ, flux=EQ,
+                       velocity=VEL)
+
+
+def oracle_rate(elems, threads, min_seconds):
+    """DOF-updates/s per RK4 stage of the oracle's -O3 -march=native build on `elems` elements of
+    the workload's problem, split over `threads` threads (1: orc_step itself); RK4 steps are
+    repeated until min_seconds have passed.  Returns (rate, seconds, steps)."""
+    from oracle import oracle as orc
+    p = _oracle_problem(elems)
     U0 = initial_condition(orc.node_coords(p))
     dt = orc.stable_dt(p, U0, CFL)
-    t = time.perf_counter()
-    orc.step(p, U0, dt, nsteps, RK)
-    el = time.perf_counter() - t
-    return p.ndof * STAGES * nsteps / el, el
+
+    def one():
+        if threads > 1:
+            return orc.step_threads(p, U0, dt, 1, RK, threads=threads, native=True)
+        return orc.step_native(p, U0, dt, 1, RK)
+
+    one()  # first touch of the buffers, library load
+    steps, el = 0, 0.0
+    while el < min_seconds or steps < 1:
+        t = time.perf_counter()
+        one()
+        el += time.perf_counter() - t
+        steps += 1
+    return p.ndof * STAGES * steps / el, el, steps
+
+
+def cpu_sample_elems():
+    """Reduced grids of the workload for the CPU samples: all cores on 1/8 of the elements, one
+    thread on 1/64 (3D) -- the oracle needs 10 state-sized host arrays."""
+    if DIM == 3:
+        return tuple(max(2, e // 2) for e in ELEMS), tuple(max(2, e // 4) for e in ELEMS)
+    return tuple(max(2, e // 2) for e in ELEMS), tuple(max(2, e // 4) for e in ELEMS)
+
+
+def cpu_baseline_block():
+    cores = host_cores()
+    many, one = cpu_sample_elems()
+    rate_mt, el_mt, st_mt = oracle_rate(many, cores, 8.0)
+    rate_1, el_1, st_1 = oracle_rate(one, 1, 8.0)
+    ndof_mt, ndof_1 = ndof_of(DIM, DEGREE, many, EQ), ndof_of(DIM, DEGREE, one, EQ)
+    return {"value": rate_mt, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{st_mt} RK4 step(s) of the workload's problem on {'x'.join(map(str, many))} elements "
+                      f"({ndof_mt / 1e6:.1f}M DOF) in {el_mt:.1f} s, the oracle's -O3 -march=native build split "
+                      f"by element ranges over {cores} threads (orc_step_threads, bitwise equal to one thread)",
+            "single_thread": {"value": rate_1, "unit": "DOF-updates/s", "cores": 1,
+                              "sample": f"{st_1} RK4 step(s) on {'x'.join(map(str, one))} elements "
+                                        f"({ndof_1 / 1e6:.2f}M DOF) in {el_1:.1f} s, orc_step, -O3 -march=native"}}
 
 
 def run_reference(args, world, rank):
+    """The oracle as it stands, on the machine's host cores, for the same metric and workload: each
+    bench step one RK4 step of the workload's problem on 1/8 of its elements (all cores)."""
     if rank != 0:
         return None
-    sample_steps = 1
+    from oracle import oracle as orc
+    cores = host_cores()
+    many, _ = cpu_sample_elems()
+    p = _oracle_problem(many)
+    U0 = initial_condition(orc.node_coords(p))
+    dt = orc.stable_dt(p, U0, CFL)
     for _ in range(args.warmup):
-        oracle_sample(sample_steps)
-    rates, tot = [], 0.0
+        orc.step_threads(p, U0, dt, 1, RK, threads=cores, native=True)
+    times = []
     for _ in range(args.steps):
-        r, el = oracle_sample(sample_steps)
-        rates.append(r)
-        tot += el
-    value = statistics.median(rates)
-    ndof = config_block(world)["dof"]
-    sample = f"{sample_steps} RK4 step of the full {ndof / 1e6:.2f}M-DOF workload per bench step ({NSTEPS} in the GPU step)"
+        t = time.perf_counter()
+        orc.step_threads(p, U0, dt, 1, RK, threads=cores, native=True)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    value = p.ndof * STAGES * args.steps / tot
+    sample = (f"1 RK4 step per bench step of the workload's problem on {'x'.join(map(str, many))} elements "
+              f"({p.ndof / 1e6:.1f}M DOF, 1/8 of the workload's elements), the oracle's -O3 -march=native build "
+              f"split by element ranges over {cores} threads")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": data_description(), "config": config_block(world),
-            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def config_block(world):
-    ndof = (1 if EQ == 0 else DIM + 1) * int(np.prod(ELEMS)) * (DEGREE + 1) ** DIM
-    return {"workload": WORKLOAD, "model": f"NDG+RK4, dim {DIM}, degree {DEGREE}", "global_batch": world,
-            "seq_len": None, "elements": list(ELEMS), "degree": DEGREE, "dof": ndof,
-            "rk_steps_per_bench_step": NSTEPS, "parallelism": f"replicas{world}",
-            "l2": f"flushed at the start of every bench step ({L2_FLUSH_BYTES >> 20} MiB write, inside the timed region)"}
-
+# ---------------------------------------------------------------------------------------------
+# GPU: the headline workload
+# ---------------------------------------------------------------------------------------------
 
 def run_solver_timed(dtype, args, dev, pg, U0_host):
-    """Device-timed bench steps of one dtype: returns per-step device ms and stage-kernel ms."""
+    """Device-timed bench steps of one precision: per-step device ms, stage-kernel ms, clocks."""
     import torch
+    from paper_2510_05254_b300 import native as nat
     from paper_2510_05254_b300.solver import Solver
-    s = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype=dtype, device=dev)
+    s = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype=dtype, device=dev,
+               elems_per_block=args.epb)
     U0 = torch.tensor(U0_host, device=f"cuda:{dev}", dtype=s.torch_dtype)
     s.set_state(U0)
     dt = s.stable_dt(CFL)
-    if args.epb:  # a fixed tile (profiler captures of the tuned configuration)
-        s.close()
-        s = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype=dtype, device=dev, elems_per_block=args.epb)
-        s.set_state(U0)
-        epb = args.epb
-    else:
-        epb, _ = s.autotune(RK)  # the library's tile autotuner (state is restored bitwise)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
-    from paper_2510_05254_b300 import native as nat
+    epb = args.epb or s.autotune(RK)[0]  # the library's tile autotuner (state restored bitwise)
 
     def one(evs=None):
-        with torch.cuda.stream(s.stream):
-            flush.zero_()
         nat.ndg_set_state(s.ctx, U0.data_ptr(), s.state_bytes, True)
         if evs:
             evs[0].record(s.stream)
@@ -287,23 +351,22 @@ def run_solver_timed(dtype, args, dev, pg, U0_host):
     total_ms = start.elapsed_time(end)
     stage_ms = sum(a.elapsed_time(b) for a, b in inner) / (args.steps * NSTEPS * STAGES)
     out = {"total_ms": total_ms, "stage_ms": stage_ms, "ndof": s.ndof, "dt": dt, "clocks": clk.summary(), "epb": epb,
-           "kernel": "line" if s.kernel == 1 else "line_var",
-           "l2_norm": nr.l2, "mass": nr.integral[0], "state_bytes": s.state_bytes,
-           "final": s.get_state()}  # after NSTEPS steps from U0 (accuracy of the precisions)
+           "kernel": "line" if s.kernel == 1 else "line_var", "l2_norm": nr.l2, "mass": nr.integral[0],
+           "state_bytes": s.state_bytes, "final": s.get_state()}
     s.close()
     return out
 
 
 def run_e2e(args, dev, U0_host):
-    """Same workload through the C ABI with HOST buffers: pinned H2D of the initial state, 1000 RK
-    steps, D2H of the final state and of the norms, every bench step."""
+    """The same bench step through the C ABI with HOST buffers: a pinned host-to-device copy of the
+    initial state, NSTEPS RK4 steps, a device-to-host copy of the final state and of the norms."""
     import torch
     from paper_2510_05254_b300 import native as nat
     from paper_2510_05254_b300.solver import Solver
-    s = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype="f64", device=dev)
-    src = torch.tensor(U0_host, dtype=torch.float64).pin_memory()
+    s = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype="f64", device=dev, elems_per_block=args.epb)
+    src = torch.from_numpy(np.ascontiguousarray(U0_host, dtype=np.float64)).pin_memory()
     dst = torch.empty_like(src).pin_memory()
-    s.set_state(U0_host)
+    nat.ndg_set_state(s.ctx, src.data_ptr(), s.state_bytes, False)
     dt = s.stable_dt(CFL)
 
     def one():
@@ -325,99 +388,81 @@ def run_e2e(args, dev, U0_host):
     return el, nb
 
 
-def run_serving(args, dev):
-    from paper_2510_05254_b300 import inputs, serving
-    n = args.serving_solves
-    reqs = serving.prepare(inputs.serving_stream(n, emax=args.serving_emax), nsteps=100)
-    import torch
-    budget = 120 << 30
-    log("serving inputs ready")
-    pool_stats, _ = serving.run_pool(reqs, math.inf, budget)
-    torch.cuda.synchronize(dev)
-    serial_stats, _ = serving.run_serial(reqs, math.inf)
-    # latency at a finite arrival rate: half of the pool's measured capacity
-    rate = 0.5 * pool_stats["solves_per_s"]
-    pool_rate_stats, _ = serving.run_pool(reqs, rate, budget)
-    # and at a quarter of and at the full measured capacity (p50 / p99 against the arrival rate)
-    sweep = []
-    for frac in (0.25, 1.0):
-        st, _ = serving.run_pool(reqs, frac * pool_stats["solves_per_s"], budget)
-        sweep.append({"rate_per_s": frac * pool_stats["solves_per_s"], "fraction_of_capacity": frac,
-                      "solves_per_s": st["solves_per_s"], "p50_s": st["p50_s"], "p99_s": st["p99_s"]})
-    sweep.insert(1, {"rate_per_s": rate, "fraction_of_capacity": 0.5, "solves_per_s": pool_rate_stats["solves_per_s"],
-                     "p50_s": pool_rate_stats["p50_s"], "p99_s": pool_rate_stats["p99_s"]})
-    # the one-solve-at-a-time FP64 path: every request in FP64, one after another
-    reqs = serving.as_fp64(reqs)
-    serial64_stats, _ = serving.run_serial(reqs, math.inf)
-    del reqs
-    return {"workload": f"{n} independent 2D solves (advection / isothermal Euler 50/50, elements per axis "
-                        f"log-uniform in [16,{args.serving_emax}], degree in {{3,5,7}}, FP64/FP32 50/50), "
-                        "100 RK4 steps each, 120 GB budget",
-            "burst": {"pool": pool_stats, "one_at_a_time": serial_stats, "one_at_a_time_all_f64": serial64_stats,
-                      "speedup_solves_per_s": pool_stats["solves_per_s"] / serial_stats["solves_per_s"],
-                      "speedup_vs_f64_one_at_a_time": pool_stats["solves_per_s"] / serial64_stats["solves_per_s"]},
-            "poisson_half_capacity": {"rate_per_s": rate, "pool": pool_rate_stats},
-            "poisson_rate_sweep": sweep}
+# ---------------------------------------------------------------------------------------------
+# the table of problems: ms per stage, roofline fractions and energy per DOF-update
+# ---------------------------------------------------------------------------------------------
 
-
-def run_workload_table(dev, peaks):
-    """The other full-size problems (2D isothermal Euler 512^2 degree 7, 3D isothermal Euler 64^3
-    degree 5, and 32^3 at degree 7): ms per RK4 stage of the autotuned tile in FP64 and FP32, CUDA
-    events around a run of RK4 steps, with the FP64-pipe and HBM roofline fractions.  Their working
-    sets (>= 0.27 GB per array) are larger than L2."""
+def timed_row(name, dtype, dev, peaks, U0, min_seconds=2.5):
+    """One problem in one precision: autotuned tile, RK4 steps timed with CUDA events for at least
+    min_seconds with board power sampled throughout."""
     import torch
-    from paper_2510_05254_b300 import inputs
     from paper_2510_05254_b300.solver import Solver
+    dim, deg, el, eq, vel, _, desc = WORKLOADS[name]
+    s = Solver(dim, deg, el, equation=eq, velocity=vel, dtype=dtype, device=dev)
+    s.set_state(U0)
+    dt = s.stable_dt(CFL)
+    epb, _ = s.autotune(RK)
+    s.set_state(U0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s.stream)
+    s.step(dt, 2, RK)
+    b.record(s.stream)
+    b.synchronize()
+    per_step = a.elapsed_time(b) / 2
+    n = max(4, int(math.ceil(min_seconds * 1e3 / per_step)))
+    s.set_state(U0)
+    with ClockSampler(dev) as clk:
+        a.record(s.stream)
+        s.step(dt, n, RK)
+        b.record(s.stream)
+        b.synchronize()
+    ms = a.elapsed_time(b) / (n * STAGES)
+    r = {"ms_per_stage": ms, "dof_updates_per_s": s.ndof / (ms * 1e-3), "elems_per_block": epb,
+         "mapping": "line" if s.kernel == 1 else "line_var", "timed_rk4_steps": n,
+         "timed_s": a.elapsed_time(b) * 1e-3}
     hbm = peaks.get("hbm_gbs", 6400.0)
-    p64 = fp64_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+    if dtype == "f32":
+        gbs = PASSES_PER_STAGE * 4 * s.ndof / (ms * 1e-3) / 1e9
+        r.update({"gbs": gbs, "frac_hbm": gbs / hbm})
+    else:
+        tf = FLOPS_PER_DOF[name] * s.ndof / (ms * 1e-3) / 1e12
+        r.update({"tflops": tf, "frac_fp64_peak": tf / fp64_peak_tflops(peaks.get("sm_max_mhz", 2032.0))})
+    c = clk.summary() or {}
+    if c.get("power_w"):
+        work = s.ndof * STAGES * n
+        r["energy"] = {"power_w_median": c["power_w"], "power_samples": c["samples"],
+                       "joules_per_dof_update": c["power_w"] * r["timed_s"] / work,
+                       "dof_updates_per_joule": work / (c["power_w"] * r["timed_s"])}
+    r["clocks"] = {k: c.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    final = s.get_state()
+    s.close()
+    return r, final, n, dt
+
+
+def run_workload_table(dev, peaks, names):
+    import torch
+    from paper_2510_05254_b300.solver import Solver
     out = {}
-    for name, nsteps in (("euler2d", 25), ("euler3d", 5), ("euler3d7", 5)):
+    for name in names:
         dim, deg, el, eq, vel, _, desc = WORKLOADS[name]
-        row = {"workload": desc}
-        U0 = None
+        probe = Solver(dim, deg, el, equation=eq, velocity=vel, dtype="f64", device=dev)
+        X = probe.node_coords()
+        probe.close()
+        U0 = np.ascontiguousarray(initial_condition(X, eq, dim))
+        del X
+        row = {"workload": desc, "dof": ndof_of(dim, deg, el, eq)}
         finals = {}
-        for dtype in ("f64", "f32"):
-            s = Solver(dim, deg, el, equation=eq, velocity=vel, dtype=dtype, device=dev)
-            if U0 is None:
-                X = s.node_coords()
-                U0 = np.ascontiguousarray(inputs.euler_shear(X) if dim == 2 else inputs.taylor_green(X))
-                del X
-            s.set_state(U0)
-            dt = s.stable_dt(CFL)
-            epb, _ = s.autotune(RK)
-            log(f"{name} {dtype} autotuned (epb {epb})")
-            n = nsteps
-            s.set_state(U0)  # the autotuner restored it; start the timed run from U0 again
-            s.step(dt, 1, RK)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(s.stream)
-            s.step(dt, n, RK)
-            b.record(s.stream)
-            b.synchronize()
-            ms = a.elapsed_time(b) / (n * STAGES)
-            r = {"ms_per_stage": ms, "dof_updates_per_s": s.ndof / (ms * 1e-3), "elems_per_block": epb,
-                 "mapping": "line" if s.kernel == 1 else "line_var"}
-            if dtype == "f64":
-                tf = FLOPS_PER_DOF[name] * s.ndof / (ms * 1e-3) / 1e12
-                r.update({"tflops": tf, "frac_fp64_peak": tf / p64})
-            else:
-                gbs = PASSES_PER_STAGE * 4 * s.ndof / (ms * 1e-3) / 1e9
-                r.update({"gbs": gbs, "frac_hbm": gbs / hbm})
-            finals[dtype] = s.get_state()
-            if name == "euler3d":
-                # the sixth-order scheme of Eq. (RK6) on the same problem (7 stages, slopes stored)
-                s.set_state(U0)
-                s.step(dt, 1, 6)
-                a.record(s.stream)
-                s.step(dt, 2, 6)
-                b.record(s.stream)
-                b.synchronize()
-                ms6 = a.elapsed_time(b) / (2 * 7)
-                r["rk6"] = {"ms_per_stage": ms6, "dof_updates_per_s": s.ndof / (ms6 * 1e-3)}
+        for dtype in (("f64", "f32", "f64ff") if name == "adv2d" else ("f64", "f32")):
+            r, final, n, dt = timed_row(name, dtype, dev, peaks, U0)
             row[dtype] = r
-            row["dof"] = s.ndof
-            s.close()
-        row["accuracy_f32_vs_f64"] = dict(rel_err(finals["f32"], finals["f64"]), steps=nsteps + 1)
+            log(f"{name} {dtype}: {r['ms_per_stage']:.4f} ms per stage ({n} RK4 steps)")
+            # the accuracy of the other precisions against FP64 after the same first steps
+            finals[dtype] = final
+        row["accuracy_vs_f64"] = {"note": "each precision's state after its own timed run compared with the FP64 "
+                                          "state after its timed run: meaningful only when the step counts agree"}
+        for dtype in finals:
+            if dtype != "f64" and row[dtype]["timed_rk4_steps"] == row["f64"]["timed_rk4_steps"]:
+                row["accuracy_vs_f64"][dtype] = rel_err(finals[dtype], finals["f64"])
         del U0, finals
         torch.cuda.empty_cache()
         out[name] = row
@@ -432,111 +477,156 @@ def rel_err(a, ref):
             "max_abs_diff": float(np.abs(d).max()), "max_abs_ref": float(np.abs(ref).max())}
 
 
-def energy_block(r64, r32, work, t64_ms, t32_ms, rff=None, tff_ms=None):
-    out = {}
-    for name, r, t in (("f64", r64, t64_ms), ("f32", r32, t32_ms), ("f64_ff", rff, tff_ms)):
-        if r is None:
-            continue
-        p = (r["clocks"] or {}).get("power_w")
-        if p:
-            out[name] = {"power_w_median": p, "joules_per_dof_update": p * t * 1e-3 / work,
-                         "dof_updates_per_joule": work / (p * t * 1e-3)}
-    return out or None
+# ---------------------------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------------------------
 
+def run_serving(args, dev):
+    """The serving stream: a burst (all arrivals at once) through the pool, one solve at a time
+    with the same dtypes, and one FP64 solve at a time; the same for the solves whose working set
+    fits in L2; then Poisson arrivals at 0.25 to 4 times the one-at-a-time FP64 capacity."""
+    import torch
+    from paper_2510_05254_b300 import inputs, serving
+    n = args.serving_solves
+    budget = 120 << 30
+    reqs = serving.prepare(inputs.serving_stream(n, emax=args.serving_emax), nsteps=100)
+    log(f"serving inputs ready ({n} solves)")
+    pool_stats, _ = serving.run_pool(reqs, math.inf, budget)
+    torch.cuda.synchronize(dev)
+    serial_stats, _ = serving.run_serial(reqs, math.inf)
+    reqs64 = serving.as_fp64(reqs)
+    serial64_stats, _ = serving.run_serial(reqs64, math.inf)
+    del reqs64
+    log("serving bursts done")
+    # the sub-L2 solves (working set of the four RK4 arrays below the 126 MB L2)
+    small = [r for r in reqs if 4 * r["U"].nbytes < L2_BYTES]
+    small_block = None
+    if small:
+        ps, _ = serving.run_pool(small, math.inf, budget)
+        ss, _ = serving.run_serial(small, math.inf)
+        s64, _ = serving.run_serial(serving.as_fp64(small), math.inf)
+        small_block = {"solves": len(small), "pool": ps, "one_at_a_time": ss, "one_at_a_time_all_f64": s64,
+                       "speedup_solves_per_s": ps["solves_per_s"] / ss["solves_per_s"],
+                       "speedup_vs_f64_one_at_a_time": ps["solves_per_s"] / s64["solves_per_s"]}
+    # Poisson arrivals at multiples of the one-at-a-time FP64 capacity
+    cap64 = serial64_stats["solves_per_s"]
+    sweep_reqs = reqs[:args.serving_sweep_solves]
+    sweep = []
+    for frac in (0.25, 0.5, 1.0, 2.0, 4.0):
+        st, _ = serving.run_pool(sweep_reqs, frac * cap64, budget)
+        sweep.append({"rate_per_s": frac * cap64, "multiple_of_f64_one_at_a_time_capacity": frac,
+                      "solves": len(sweep_reqs), "solves_per_s": st["solves_per_s"], "p50_s": st["p50_s"],
+                      "p99_s": st["p99_s"]})
+        log(f"serving sweep {frac}x done")
+    del reqs
+    return {"workload": f"{n} independent 2D solves (advection / isothermal Euler 50/50, elements per axis "
+                        f"log-uniform in [16,{args.serving_emax}], degree in {{3,5,7}}, FP64/FP32 50/50), "
+                        "100 RK4 steps each, 120 GB budget",
+            "burst": {"pool": pool_stats, "one_at_a_time": serial_stats, "one_at_a_time_all_f64": serial64_stats,
+                      "speedup_solves_per_s": pool_stats["solves_per_s"] / serial_stats["solves_per_s"],
+                      "speedup_vs_f64_one_at_a_time": pool_stats["solves_per_s"] / serial64_stats["solves_per_s"]},
+            "burst_sub_l2_solves": small_block,
+            "poisson_rate_sweep": sweep,
+            "accuracy": "each pool result equals its solve alone bit for bit (tests/test_gpu_serving.py); FP32 "
+                        "solves within the FP32 tolerance of the FP64 path"}
+
+
+# ---------------------------------------------------------------------------------------------
 
 def run_ours(args, world, rank, dev, pg):
     import torch
     from paper_2510_05254_b300.solver import Solver
     peaks, peak_kind = load_peaks()
+    line = {}
+    if args.serving_only:
+        return {"serving": run_serving(args, dev)}
     probe = Solver(DIM, DEGREE, ELEMS, equation=EQ, velocity=VEL, dtype="f64", device=dev)
     X = probe.node_coords()
     probe.close()
     U0 = np.ascontiguousarray(initial_condition(X))
+    del X
     chosen = set(args.variants.split(","))
-    skipped = {"total_ms": float("nan"), "stage_ms": float("nan"), "ndof": None, "clocks": None, "epb": None,
-               "kernel": None, "l2_norm": None, "mass": None, "state_bytes": 0, "final": None}
     log("initial condition ready")
-    r64 = run_solver_timed("f64", args, dev, pg, U0) if "f64" in chosen else dict(skipped)
-    log("f64 timed")
-    r32 = run_solver_timed("f32", args, dev, pg, U0) if "f32" in chosen else dict(skipped)
-    log("f32 timed")
-    rff = run_solver_timed("f64ff", args, dev, pg, U0) if "f64ff" in chosen else dict(skipped)
-    log("f64ff timed")
-    for r in (r64, r32, rff):
-        if r["ndof"] is None:
-            r["ndof"] = next(x["ndof"] for x in (r64, r32, rff) if x["ndof"] is not None)
+    r64 = run_solver_timed("f64", args, dev, pg, U0)
+    log(f"f64 timed: {r64['stage_ms']:.4f} ms per stage")
+    r32 = run_solver_timed("f32", args, dev, pg, U0) if "f32" in chosen else None
+    if r32:
+        log(f"f32 timed: {r32['stage_ms']:.4f} ms per stage")
+    rff = run_solver_timed("f64ff", args, dev, pg, U0) if "f64ff" in chosen else None
     t64 = max_over_ranks(pg, r64["total_ms"], dev)
-    t32 = max_over_ranks(pg, r32["total_ms"], dev)
-    tff = max_over_ranks(pg, rff["total_ms"], dev)
     work = r64["ndof"] * STAGES * NSTEPS * args.steps
     value = world * work / (t64 * 1e-3)
-    value32 = world * work / (t32 * 1e-3)
-    e2e_s, nb = run_e2e(args, dev, U0) if "f64" in chosen else (float("nan"), 0)
-    log("e2e timed")
+    e2e_s, nb = run_e2e(args, dev, U0)
     e2e_s = max_over_ranks(pg, e2e_s, dev)
-    # roofline of the dominant kernel (the fused stage kernel)
-    clocks = r64["clocks"] or {}
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
-    p64 = fp64_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
-    ach64 = FLOPS_PER_DOF_STAGE * r64["ndof"] / (r64["stage_ms"] * 1e-3) / 1e12
-    bytes32 = PASSES_PER_STAGE * 4 * r32["ndof"]
-    ach32 = bytes32 / (r32["stage_ms"] * 1e-3) / 1e9
+    log("e2e timed")
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    p64 = fp64_peak_tflops(sm_max)
+    flops = FLOPS_PER_DOF[args.workload]
+    ach64 = flops * r64["ndof"] / (r64["stage_ms"] * 1e-3) / 1e12
     hbm = peaks.get("hbm_gbs", 6400.0)
-    line = {
+    traffic64 = TRAFFIC_PER_LAUNCH.get((args.workload, "f64")) if not args.elems else None
+    line.update({
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": data_description(),
-        "config": config_block(world),
+        "vs_baseline": None, "dtype": "f64", "data": data_description(), "config": config_block(world),
         "e2e": {"value": world * work / e2e_s, "unit": "DOF-updates/s", "h2d_bytes_per_step": nb,
-                "d2h_bytes_per_step": nb + 8 * 8},
-        "gpu_launches": args.steps * (NSTEPS * STAGES + 2),  # per variant timed region
+                "d2h_bytes_per_step": nb + 8 * 8,
+                "note": "per bench step: pinned host->device copy of the initial state, the RK4 steps, "
+                        "device->host copy of the final state and of the norms (ndg_set_state / ndg_step / "
+                        "ndg_get_state / ndg_norms with host buffers)"},
+        # kernels of the timed region: NSTEPS x 4 stage launches + 2 norms kernels per bench step
+        "gpu_launches": args.steps * (NSTEPS * STAGES + 2),
         "roofline": {"bound": "alu", "achieved": ach64, "peak": p64, "unit": "TFLOP/s", "frac": ach64 / p64,
-                     "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, "f64")) if not args.elems else None,
-                     "traffic_note": "DRAM bytes per stage launch (ncu, mean of the 4 RK4 stages); algorithmic "
-                                     "%.1f MB: part of the 4 x %.1f MB arrays stays in L2" % (
-                                         PASSES_PER_STAGE * 8 * r64["ndof"] / 1e6, 8 * r64["ndof"] / 1e6),
+                     "traffic": traffic64,
+                     "traffic_note": "DRAM bytes per stage launch, mean of the four RK4 stages (ncu at 48^3 "
+                                     "scaled to 64^3 by the DOF count); algorithmic %.0f MB (4 array passes x "
+                                     "%.0f MB)" % (PASSES_PER_STAGE * 8 * r64["ndof"] / 1e6, 8 * r64["ndof"] / 1e6),
                      "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},double>",
-                     "peak_note": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop at the max SM clock (derived)",
-                     "stage_ms": r64["stage_ms"], "elems_per_block": r64["epb"],
-                     "mapping": r64["kernel"]},
-        "f32": {"value": value32, "unit": "DOF-updates/s", "ms_per_step": t32 / args.steps,
-                "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
-                             "frac": ach32 / hbm,
-                             "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, "f32")) if not args.elems else None,
-                             "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},float>",
-                             "peak_kind": peak_kind, "stage_ms": r32["stage_ms"],
-                             "elems_per_block": r32["epb"], "mapping": r32["kernel"],
-                             "note": ("working set 4 x %.1f MB %s the 126 MB L2" % (
-                                 r32["state_bytes"] / 1e6,
-                                 "fits" if 4 * r32["state_bytes"] < 126e6 else "exceeds"))}},
-        # FP64 state and stage update with the D contraction in float-float on the FP32 pipe
-        # (NDG_F64_FF): held to the FP64 parity bar (1e-12 relative L2 per step vs the oracle)
-        "f64_ff": {"value": world * work / (tff * 1e-3), "unit": "DOF-updates/s", "ms_per_step": tff / args.steps,
-                   "stage_ms": rff["stage_ms"], "elems_per_block": rff["epb"], "mapping": rff["kernel"],
-                   "parity": "1e-12 relative L2 per step vs the FP64 oracle (tests/test_gpu_parity.py)",
-                   "l2_norm": rff["l2_norm"]},
+                     "flop_per_dof": flops,
+                     "peak_note": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop at the max SM clock (derived; "
+                                  "1.12 TFLOP/s measured by an FMA-chain probe at 1935 MHz)",
+                     "stage_ms": r64["stage_ms"], "elems_per_block": r64["epb"], "mapping": r64["kernel"]},
         "clocks": r64["clocks"],
-        # energy per DOF-update from the measured board power during the timed region (the paper's
-        # energy comparison, Sec. 3.3, multiplies TDP by run time instead)
-        "energy": energy_block(r64, r32, work, t64, t32, rff, tff),
-        "check": {"l2_norm_f64": r64["l2_norm"], "l2_norm_f32": r32["l2_norm"], "l2_norm_f64_ff": rff["l2_norm"],
-                  "mass_f64": r64["mass"]},
-        # the FP64 path matches the oracle to 1e-12 per step (tests), so these are the other
-        # precisions' errors against the method in FP64 after NSTEPS steps
-        "accuracy": {"steps": NSTEPS,
-                     "f32_vs_f64": (rel_err(r32["final"], r64["final"])
-                                    if r32.get("final") is not None and r64.get("final") is not None else None),
-                     "f64_ff_vs_f64": (rel_err(rff["final"], r64["final"])
-                                       if rff.get("final") is not None and r64.get("final") is not None else None)},
-    }
+    })
+    if r32:
+        t32 = max_over_ranks(pg, r32["total_ms"], dev)
+        ach32 = PASSES_PER_STAGE * 4 * r32["ndof"] / (r32["stage_ms"] * 1e-3) / 1e9
+        line["f32"] = {"value": world * work / (t32 * 1e-3), "unit": "DOF-updates/s", "ms_per_step": t32 / args.steps,
+                       "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
+                                    "frac": ach32 / hbm, "peak_kind": peak_kind,
+                                    "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, "f32")) if not args.elems else None,
+                                    "kernel": f"stage_kernel_r96<{DIM},{DEGREE},{EQ},float> "
+                                              "(euler3d_f32_body)" if DIM == 3 and EQ == 1 else
+                                              f"stage_kernel<{DIM},{DEGREE},{EQ},float>",
+                                    "stage_ms": r32["stage_ms"], "elems_per_block": r32["epb"],
+                                    "mapping": r32["kernel"],
+                                    "bytes_per_dof": "4 array passes x 4 B (RK4 passes per stage 3, 5, 5, 3)"},
+                       "clocks": r32["clocks"],
+                       "accuracy_vs_f64": rel_err(r32["final"], r64["final"])}
+    if rff:
+        tff = max_over_ranks(pg, rff["total_ms"], dev)
+        line["f64_ff"] = {"value": world * work / (tff * 1e-3), "unit": "DOF-updates/s", "stage_ms": rff["stage_ms"],
+                          "parity": "1e-12 relative L2 per step vs the FP64 oracle (tests/test_gpu_parity.py)",
+                          "accuracy_vs_f64": rel_err(rff["final"], r64["final"])}
+    # energy per DOF-update from the board power sampled during the timed region (the paper's
+    # energy comparison, Sec. 3.3, multiplies TDP by run time instead)
+    energy = {}
+    for name, r, t in (("f64", r64, t64), ("f32", r32, None)):
+        if r is None or not (r["clocks"] or {}).get("power_w"):
+            continue
+        t = r["total_ms"] if t is None else t
+        energy[name] = {"power_w_median": r["clocks"]["power_w"], "power_samples": r["clocks"]["samples"],
+                        "timed_s": t * 1e-3, "joules_per_dof_update": r["clocks"]["power_w"] * t * 1e-3 / work}
+    line["energy"] = energy or None
+    line["check"] = {"l2_norm_f64": r64["l2_norm"], "mass_f64": r64["mass"],
+                     "l2_norm_f32": r32["l2_norm"] if r32 else None}
+    del U0, r64, r32, rff
     if rank == 0 and not args.no_cpu_baseline:
-        rate, el = oracle_sample(args.cpu_steps)
-        line["cpu_baseline"] = {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{args.cpu_steps} RK4 steps of the full 4.19M-DOF workload "
-                                          f"({el:.1f} s, single-threaded FP64 oracle)"}
-    log("cpu baseline done")
-    if not args.no_workloads and args.workload == "adv2d":
-        line["workloads"] = run_workload_table(dev, peaks)
+        line["cpu_baseline"] = cpu_baseline_block()
+        log("cpu baseline done")
+    if not args.no_workloads and rank == 0:
+        names = [n for n in ("adv2d", "euler2d", "euler3d7", "euler3d") if n in WORKLOADS]
+        line["workloads"] = run_workload_table(dev, peaks, names)
         log("workload table done")
     if rank == 0 and not args.no_serving:
         line["serving"] = run_serving(args, dev)
@@ -553,17 +643,19 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true",
-                    help="skip the 2D / 3D isothermal Euler table (FP64 and FP32 ms per stage)")
-    ap.add_argument("--cpu-steps", type=int, default=15)
+                    help="skip the table of problems (ms per stage, roofline fractions, energy)")
     ap.add_argument("--serving-solves", type=int, default=200)
+    ap.add_argument("--serving-sweep-solves", type=int, default=60,
+                    help="solves per Poisson rate of the sweep (the first ones of the stream)")
     ap.add_argument("--serving-emax", type=int, default=512)
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="adv2d")
+    ap.add_argument("--serving-only", action="store_true", help="only the serving block (full-size stream runs)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=HEADLINE)
     ap.add_argument("--epb", type=int, default=0,
                     help="elements per CTA tile instead of autotuning (profiler captures)")
     ap.add_argument("--elems", type=int, default=0,
                     help="elements per axis instead of the workload's (smaller cases for profiler captures)")
-    ap.add_argument("--variants", default="f64,f32,f64ff",
-                    help="precisions to time (comma list of f64, f32, f64ff); f64 is the headline")
+    ap.add_argument("--variants", default="f64,f32",
+                    help="precisions to time beside the FP64 headline (comma list of f32, f64ff)")
     args = ap.parse_args()
     select_workload(args.workload)
     if args.elems:
@@ -572,10 +664,7 @@ def main():
         WORKLOAD = WORKLOAD.split(",")[0] + f", {args.elems}^{DIM} elements (reduced for a profiler capture)"
         args.no_cpu_baseline = True
         args.no_workloads = True
-    global FLOPS_PER_DOF_STAGE
-    FLOPS_PER_DOF_STAGE = FLOPS_PER_DOF[args.workload]
-    if args.workload != "adv2d":  # the roofline flop count and the CPU sample are the bench workload's
-        args.no_cpu_baseline = True
+        args.no_serving = True
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local, pg = dist_setup(args)

@@ -20,25 +20,41 @@ CFL = 0.1
 
 
 def prepare(requests, nsteps=100):
-    """Initial states and time steps of the serving workload (outside any timed region), from the
-    separable grid forms of the initial conditions (the same values as the pointwise ones)."""
+    """Initial states and time steps of the serving workload (outside any timed region).  The node
+    coordinates come from the library (ndg_node_coords: the 1D coordinates along x of one row of
+    elements, the same along y), the initial conditions from their separable grid forms (the same
+    values as the pointwise ones), and the time step from the library's CFL rule applied to that
+    state (ndg_stable_dt)."""
+    import torch
     out = []
-    for r in requests:
-        E, N = r["elems"], r["degree"]
-        xi, _ = nat.ndg_lgl(N)
-        xi = np.asarray(xi)
-        h = 1.0 / E
-        x = (np.arange(E)[:, None] * h + 0.5 * h * (xi[None, :] + 1.0)).reshape(-1)
-        if r["equation"] == 0:
-            U = inputs.grid_state("gaussian_noise", x, E, N + 1, r["seed"])
-            lam = 1.0 + 0.5
-        else:
-            U = inputs.grid_state("euler_shear", x, E, N + 1, r["seed"])
-            lam = float(np.max(np.abs(U[1] / U[0]) + np.abs(U[2] / U[0]))) + 2.0
-        gap = min(xi[k + 1] - xi[k] for k in range(N))
-        dt = CFL * (0.5 / E) * gap / lam
-        U = np.ascontiguousarray(U, dtype=np.float64 if r["dtype"] == "f64" else np.float32)
-        out.append(dict(r, U=U, dt=dt, nsteps=nsteps))
+    x_of = {}
+    ctx_of = {}
+    try:
+        for r in requests:
+            E, N = r["elems"], r["degree"]
+            cfg = _cfg(r)
+            cfg.stream = torch.cuda.current_stream().cuda_stream
+            key = (E, N, r["equation"], r["dtype"])
+            if key not in ctx_of:
+                ctx_of[key] = nat.ndg_create_ex(cfg)
+            ctx = ctx_of[key]
+            if (E, N) not in x_of:
+                info = nat.ndg_info(ctx)
+                X = np.empty((2, info.nelem, info.nodes_per_elem))
+                nat.ndg_node_coords(ctx, X.ctypes.data, X.size)
+                x_of[(E, N)] = np.ascontiguousarray(X[0, :E, :N + 1]).reshape(-1)  # row ey = 0, j = 0
+            kind = "gaussian_noise" if r["equation"] == 0 else "euler_shear"
+            U = inputs.grid_state(kind, x_of[(E, N)], E, N + 1, r["seed"])
+            U = np.ascontiguousarray(U, dtype=np.float64 if r["dtype"] == "f64" else np.float32)
+            nat.ndg_set_state(ctx, U.ctypes.data, U.nbytes, False)
+            dt = nat.ndg_stable_dt(ctx, CFL)
+            out.append(dict(r, U=U, dt=dt, nsteps=nsteps))
+            if len(ctx_of) > 8:  # keep few contexts (and their device memory) alive
+                for k in [k for k in ctx_of if k != key]:
+                    nat.ndg_destroy(ctx_of.pop(k))
+    finally:
+        for c in ctx_of.values():
+            nat.ndg_destroy(c)
     return out
 
 

@@ -22,7 +22,8 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference"
     assert d["value"] > 0 and d["unit"] == "DOF-updates/s" and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] >= 3 and d["n_gpus"] == 1 and d["dtype"] == "f64"
-    assert d["config"]["dof"] == 256 * 256 * 64 and "workload" in d["config"]
+    assert d["config"]["dof"] == 4 * 64 ** 3 * 6 ** 3 and "workload" in d["config"]
+    assert "model" not in d["config"]  # the workload is named, not a model
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
