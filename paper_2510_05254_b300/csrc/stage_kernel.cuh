@@ -494,7 +494,15 @@ struct StageGeom {
   // float-float lose occupancy), so 3D and float-float load each axis's traces in its pass (and
   // the FP64 / float-float update there goes one node at a time; FP32 3D moves quads).
   static constexpr int NS = (EQ == 0 || SLIM) ? 2 * NV : 2 * NV + DIM;  // shared arrays of SPE per element
-  static constexpr int NB = SLIM ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
+  // GOPS: the update reads U^n / ACC from global memory (after an L2 prefetch issued with the
+  // tile) instead of copies staged in shared memory.  FP32 always; FP64 in 3D at degree 7 with one
+  // thread per line, where the staged copies take 32 of an Euler element's 84 KB of shared memory
+  // and with them half the CTAs an SM holds (measured: 32^3 FP64 5.16 -> 4.36 ms per stage; at
+  // degree 5, where registers bind first, 16.07 -> 16.19, so it keeps them).  The
+  // line-and-variable mapping keeps them too: the global loads cost registers its large CTAs do
+  // not have.
+  static constexpr bool GOPS = SLIM || (DIM == 3 && !VS && N == 7);
+  static constexpr int NB = GOPS ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
   static constexpr int TPE = VS ? L * NV : L;
   __device__ static __forceinline__ int pad(int node) {
@@ -527,7 +535,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   // U^n / ACC reach L2 by bulk prefetches (16-byte aligned ranges: the arrays are 256-byte
   // aligned).  Measured on the 16-byte 2D layouts: Euler degree 7 170 -> 167 us, advection
   // degree 3 19.6 -> 20.8 us, so advection there keeps the per-line prefetches.
-  constexpr bool BPF = G::SLIM && (NPE * sizeof(real)) % 16 == 0 && (G::BULK || EQ == 1);
+  constexpr bool BPF = G::GOPS && (NPE * sizeof(real)) % 16 == 0 && (G::BULK || EQ == 1 || !G::SLIM);
   // 2D FP64: the y-line threads own whole lines of finished right-hand side and apply the stage
   // update to them directly (no shared round trip, one barrier less: 2D Euler 2.40 -> 2.28 ms per
   // stage).  Elsewhere the extra registers cost more occupancy than the round trip does (measured:
@@ -594,7 +602,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
             cp_async_elem(dst + el * SPE + G::pad(node), src + idx);
           }
         }
-        if constexpr (G::SLIM) {
+        if constexpr (G::GOPS) {
           // start the update's reads now: one L2 prefetch per 128-byte line of U^n / ACC (BPF:
           // one bulk prefetch per array, below)
           if constexpr (!BPF) {
@@ -775,8 +783,8 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
           for (int l = 0; l < n; ++l) {
             if (plan.acc_mode != 3)
               bb[l] = plan.in == kUN ? sUe[v * epb * SPE + l * pstride]
-                                     : (G::SLIM ? S.un[g0 + l * ustride] : sB[v * epb * NPE + bline + l * ustride]);
-            if (plan.acc_mode >= 2) aa[l] = G::SLIM ? S.acc[g0 + l * ustride] : sA[v * epb * NPE + bline + l * ustride];
+                                     : (G::GOPS ? S.un[g0 + l * ustride] : sB[v * epb * NPE + bline + l * ustride]);
+            if (plan.acc_mode >= 2) aa[l] = G::GOPS ? S.acc[g0 + l * ustride] : sA[v * epb * NPE + bline + l * ustride];
           }
         };
         // The right-hand side is kept divided by axis 0's scale (rhs_scale), so axis 0 needs no
@@ -1000,7 +1008,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
       const int total = cnt * NPE;
       // each thread owns up to B nodes per variable: all of their operands are loaded first, so
       // the loads are in flight together, then the results are computed and stored
-      constexpr int B = EARLY ? 8 : 1;
+      constexpr int B = EARLY ? 8 : (G::GOPS ? 2 : 1);  // (GOPS FP64: 4 cost registers, no time)
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const real* sRv = sR + v * epb * SPE;
@@ -1018,8 +1026,8 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
             const int s = el * SPE + G::pad(node);
             const long long g = goff + idx;
             rr[k] = sRv[s];
-            if (plan.acc_mode >= 2) aa[k] = G::SLIM ? S.acc[g] : sAv[idx];
-            if (plan.acc_mode != 3) bb[k] = plan.in == kUN ? sUv[s] : (G::SLIM ? S.un[g] : sBv[idx]);
+            if (plan.acc_mode >= 2) aa[k] = G::GOPS ? S.acc[g] : sAv[idx];
+            if (plan.acc_mode != 3) bb[k] = plan.in == kUN ? sUv[s] : (G::GOPS ? S.un[g] : sBv[idx]);
           }
 #pragma unroll
           for (int k = 0; k < B; ++k) {
