@@ -149,6 +149,15 @@ int ndg_get_state(ndg_ctx* ctx, void* dst, size_t nbytes, int dst_on_device, int
  * finite, nsteps < 0, unknown rk), NDG_ESTATE (no state set), NDG_ECUDA. */
 int ndg_step(ndg_ctx* ctx, double dt, int nsteps, int rk_scheme);
 
+/* The same steps as ndg_step, for verification: every RK stage runs in split form -- per axis a
+ * volume-term kernel (sum-factorised D, Sec. 2.1) and a surface-term kernel (numerical flux of
+ * Eq. (LF) lifted by the lumped mass), then the stage-update kernel (Eq. (RK3)/(RK4)/(RK6)) --
+ * over a state-sized right-hand-side array the context allocates on first use.  The operations
+ * are the fused kernel's in the same order, so the result equals ndg_step's bit for bit.  No
+ * graph, no tiles; slower.  NDG_F64 and NDG_F32 with the lumped mass (NDG_EINVAL otherwise);
+ * other errors as ndg_step. */
+int ndg_step_split(ndg_ctx* ctx, double dt, int nsteps, int rk_scheme);
+
 /* Norms of the state, or of state - ref when ref is not NULL (ref has the context's dtype and
  * element layout, on the host if ref_on_device = 0, else on the device).  FP64 accumulation,
  * deterministic (fixed reduction order, no atomics).  Waits for the result.  Returns

@@ -913,6 +913,32 @@ int ndg_step(ndg_ctx* c, double dt, int nsteps, int rk) {
   return NDG_OK;
 }
 
+int ndg_step_split(ndg_ctx* c, double dt, int nsteps, int rk) {
+  if (!c) return fail(NDG_EINVAL, "NULL context");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(NDG_EINVAL, "dt must be positive and finite");
+  if (nsteps < 0) return fail(NDG_EINVAL, "nsteps must be >= 0");
+  if (!valid_rk(rk)) return fail(NDG_EINVAL, "rk_scheme must be 3, 4 or 6 (got %d)", rk);
+  if (c->kc.dtype == NDG_F64_FF || c->kc.mass == NDG_MASS_EXACT)
+    return fail(NDG_EINVAL, "the split stage is built for NDG_F64 and NDG_F32 with the lumped mass");
+  if (!c->have_state) return fail(NDG_ESTATE, "no state has been set");
+  if (nsteps == 0) return NDG_OK;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard dg(c->cfg.device);
+  int rc = ensure_buffers(c, rk);
+  if (rc == NDG_OK) rc = ensure_scratch(c);  // the right-hand side between the kernels
+  if (rc) return rc;
+  SolveDesc d = c->desc;
+  d.dt = dt;
+  for (int s = 0; s < nsteps; ++s)
+    for (const StagePlan& p : stage_plans(rk)) {
+      const int e = launch_split_stage(c->kc, d, p, c->d_scratch, c->stream);
+      if (e != 0) return cuda_fail((cudaError_t)e, "split stage launch");
+    }
+  c->t += dt * nsteps;
+  c->steps += nsteps;
+  return NDG_OK;
+}
+
 int ndg_norms(ndg_ctx* c, const void* ref, int ref_on_device, ndg_norms_t* out) {
   if (!c || !out) return fail(NDG_EINVAL, "NULL argument");
   if (!c->have_state) return fail(NDG_ESTATE, "no state has been set");

@@ -121,6 +121,10 @@ struct KernelClass {
 // Returns a cudaError_t value.
 int launch_stage(const KernelClass& kc, int variant, int grid, int epb, const SolveDesc* solves,
                  const GroupHeader* header, const StagePlan& plan, void* stream);
+// One RK stage in split form (per axis a volume-term and a surface-term kernel, then the update
+// kernel) over the right-hand-side array R (state-sized, the class's precision); the fused
+// kernel's operations in the same order.  FP64 / FP32, lumped mass.  Returns a cudaError_t value.
+int launch_split_stage(const KernelClass& kc, const SolveDesc& sd, const StagePlan& plan, void* R, void* stream);
 // Records the shape of a failed stage launch; appended to the next error message.
 void launch_error_detail(int grid, int threads, size_t smem, int max_threads, int regs, size_t local,
                          int max_dyn_smem);

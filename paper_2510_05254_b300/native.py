@@ -72,6 +72,7 @@ _SIGS = {
     "ndg_set_state": [_P, _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int],
     "ndg_get_state": [_P, _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int],
     "ndg_step": [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int],
+    "ndg_step_split": [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int],
     "ndg_norms": [_P, _P, ctypes.c_int, ctypes.POINTER(ndg_norms_t)],
     "ndg_stable_dt": [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     "ndg_norms_noalloc": [ctypes.POINTER(ndg_config), _P, _P, ctypes.c_int, _P, _P],
@@ -180,6 +181,11 @@ def ndg_get_state(ctx, ptr: int, nbytes: int, on_device: bool, layout: int = NDG
 
 def ndg_step(ctx, dt: float, nsteps: int, rk: int = NDG_RK4) -> None:
     _call("ndg_step", ctx, float(dt), int(nsteps), int(rk))
+
+
+def ndg_step_split(ctx, dt: float, nsteps: int, rk: int = NDG_RK4) -> None:
+    """ndg_step with every stage in split form (volume / surface / update kernels): verification."""
+    _call("ndg_step_split", ctx, float(dt), int(nsteps), int(rk))
 
 
 def ndg_norms(ctx, ref_ptr=None, ref_on_device: bool = False, allow_nonfinite: bool = False) -> ndg_norms_t:
