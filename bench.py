@@ -66,8 +66,30 @@ FLOPS_PER_DOF = {"adv2d": 40.0, "euler2d": 48.0, "euler3d": 60.0, "euler3d7": 72
 # DRAM bytes (read + write) per stage launch of the headline's kernels, mean of the four RK4
 # stages, from ncu captures of dram__bytes_read.sum + dram__bytes_write.sum at 48^3 elements
 # scaled to 64^3 by the DOF count (commands and per-stage values in
-# profiles/stage_kernel_euler3d_deg5_64cubed.md); to be captured again when a kernel changes.
+# profiles/stage_kernel_euler3d_deg5_64cubed.md).  The figures hold for the kernel sources they
+# were captured from: TRAFFIC_SOURCES_SHA1 is the digest of those files at the capture, and a
+# bench run whose sources differ reports traffic null until the capture is repeated.
 TRAFFIC_PER_LAUNCH = {("euler3d", "f64"): 7.3295e9, ("euler3d", "f32"): 3.5634e9}
+TRAFFIC_SOURCES = ["stage_kernel.cuh", "stage_euler3d_f32.cuh", "stage_dispatch.cuh", "stage_f64_d3.cu",
+                   "stage_f32_d3.cu", "ndg_internal.h"]
+TRAFFIC_SOURCES_SHA1 = ""
+
+
+def kernel_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2510_05254_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(workload, dtype, reduced):
+    """The captured DRAM bytes per launch, or None (a reduced problem, no capture for this
+    workload, or kernel sources changed since the capture)."""
+    if reduced or kernel_sources_sha1() != TRAFFIC_SOURCES_SHA1:
+        return None
+    return TRAFFIC_PER_LAUNCH.get((workload, dtype))
 L2_BYTES = 126e6
 
 _T0 = time.perf_counter()
@@ -564,7 +586,7 @@ def run_ours(args, world, rank, dev, pg):
     flops = FLOPS_PER_DOF[args.workload]
     ach64 = flops * r64["ndof"] / (r64["stage_ms"] * 1e-3) / 1e12
     hbm = peaks.get("hbm_gbs", 6400.0)
-    traffic64 = TRAFFIC_PER_LAUNCH.get((args.workload, "f64")) if not args.elems else None
+    traffic64 = traffic_per_launch(args.workload, "f64", bool(args.elems))
     line.update({
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -579,8 +601,11 @@ def run_ours(args, world, rank, dev, pg):
         "roofline": {"bound": "alu", "achieved": ach64, "peak": p64, "unit": "TFLOP/s", "frac": ach64 / p64,
                      "traffic": traffic64,
                      "traffic_note": "DRAM bytes per stage launch, mean of the four RK4 stages (ncu at 48^3 "
-                                     "scaled to 64^3 by the DOF count); algorithmic %.0f MB (4 array passes x "
-                                     "%.0f MB)" % (PASSES_PER_STAGE * 8 * r64["ndof"] / 1e6, 8 * r64["ndof"] / 1e6),
+                                     "scaled to 64^3 by the DOF count; null when the kernel sources differ from "
+                                     "the captured ones or the problem is reduced); algorithmic %.0f MB (4 array "
+                                     "passes x %.0f MB)" % (PASSES_PER_STAGE * 8 * r64["ndof"] / 1e6,
+                                                            8 * r64["ndof"] / 1e6),
+                     "kernel_sources_sha1": kernel_sources_sha1(),
                      "kernel": f"stage_kernel<{DIM},{DEGREE},{EQ},double>",
                      "flop_per_dof": flops,
                      "peak_note": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop at the max SM clock (derived; "
@@ -594,7 +619,7 @@ def run_ours(args, world, rank, dev, pg):
         line["f32"] = {"value": world * work / (t32 * 1e-3), "unit": "DOF-updates/s", "ms_per_step": t32 / args.steps,
                        "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s",
                                     "frac": ach32 / hbm, "peak_kind": peak_kind,
-                                    "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, "f32")) if not args.elems else None,
+                                    "traffic": traffic_per_launch(args.workload, "f32", bool(args.elems)),
                                     "kernel": f"stage_kernel_r96<{DIM},{DEGREE},{EQ},float> "
                                               "(euler3d_f32_body)" if DIM == 3 and EQ == 1 else
                                               f"stage_kernel<{DIM},{DEGREE},{EQ},float>",

@@ -29,3 +29,18 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_is_reported_only_for_the_captured_kernel_sources(monkeypatch):
+    """roofline.traffic comes from an ncu capture of given kernel sources: the bench reports it
+    only while the sources are those (digest), and never for a reduced problem."""
+    sys.path.insert(0, ROOT)
+    import bench
+    digest = bench.kernel_sources_sha1()
+    assert len(digest) == 40
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA1", digest)
+    assert bench.traffic_per_launch("euler3d", "f64", False) == bench.TRAFFIC_PER_LAUNCH[("euler3d", "f64")]
+    assert bench.traffic_per_launch("euler3d", "f64", True) is None
+    assert bench.traffic_per_launch("adv2d", "f64", False) is None
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA1", "0" * 40)
+    assert bench.traffic_per_launch("euler3d", "f32", False) is None
