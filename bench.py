@@ -474,7 +474,7 @@ def run_workload_table(dev, peaks, names):
         del X
         row = {"workload": desc, "dof": ndof_of(dim, deg, el, eq)}
         finals = {}
-        for dtype in (("f64", "f32", "f64ff") if name == "adv2d" else ("f64", "f32")):
+        for dtype in (("f64", "f32", "f64ff") if name in ("adv2d", "euler3d") else ("f64", "f32")):
             r, final, n, dt = timed_row(name, dtype, dev, peaks, U0)
             row[dtype] = r
             log(f"{name} {dtype}: {r['ms_per_stage']:.4f} ms per stage ({n} RK4 steps)")
@@ -630,7 +630,11 @@ def run_ours(args, world, rank, dev, pg):
                        "accuracy_vs_f64": rel_err(r32["final"], r64["final"])}
     if rff:
         tff = max_over_ranks(pg, rff["total_ms"], dev)
+        achff = flops * rff["ndof"] / (rff["stage_ms"] * 1e-3) / 1e12
         line["f64_ff"] = {"value": world * work / (tff * 1e-3), "unit": "DOF-updates/s", "stage_ms": rff["stage_ms"],
+                          "elems_per_block": rff["epb"], "mapping": rff["kernel"],
+                          "fp64_equivalent_tflops": achff, "frac_fp64_peak": achff / p64,
+                          "note": "FP64 state, fluxes and update; the D contraction in float-float (FP32 pipe)",
                           "parity": "1e-12 relative L2 per step vs the FP64 oracle (tests/test_gpu_parity.py)",
                           "accuracy_vs_f64": rel_err(rff["final"], r64["final"])}
     # energy per DOF-update from the board power sampled during the timed region (the paper's
@@ -679,7 +683,7 @@ def main():
                     help="elements per CTA tile instead of autotuning (profiler captures)")
     ap.add_argument("--elems", type=int, default=0,
                     help="elements per axis instead of the workload's (smaller cases for profiler captures)")
-    ap.add_argument("--variants", default="f64,f32",
+    ap.add_argument("--variants", default="f64,f32,f64ff",
                     help="precisions to time beside the FP64 headline (comma list of f32, f64ff)")
     args = ap.parse_args()
     select_workload(args.workload)

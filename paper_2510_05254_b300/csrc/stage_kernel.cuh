@@ -453,7 +453,7 @@ __device__ __noinline__ void flag_failure(const StageArgs<real>& args) {
     if (args.solves[i].status) atomicExch(args.solves[i].status, kStageErrBulkWait);
 }
 
-template <int DIM, int N, int EQ, typename real, bool VS = false>
+template <int DIM, int N, int EQ, typename real, bool VS = false, bool FF = false>
 struct StageGeom {
   static constexpr int n = N + 1;
   static constexpr int L = ipow_c(n, DIM - 1);      // lines per element along one axis
@@ -500,8 +500,12 @@ struct StageGeom {
   // and with them half the CTAs an SM holds (measured: 32^3 FP64 5.16 -> 4.36 ms per stage; at
   // degree 5, where registers bind first, 16.07 -> 16.19, so it keeps them).  The
   // line-and-variable mapping keeps them too: the global loads cost registers its large CTAs do
-  // not have.
-  static constexpr bool GOPS = SLIM || (DIM == 3 && !VS && N == 7);
+  // not have.  Float-float 3D Euler at degree 5 with one thread per line: with its registers
+  // capped at 168 (FF3D_REGS) shared memory binds, and without the staged copies three CTAs of
+  // three elements fit an SM instead of one of six (measured at 64^3: 17.07 -> 14.91 ms per
+  // stage; FP64 16.10).  At degree 7 and in 2D the same changes measured slower.
+  static constexpr bool FF3D = FF && DIM == 3 && EQ == 1 && N == 5 && !VS;
+  static constexpr bool GOPS = SLIM || (DIM == 3 && !VS && N == 7) || FF3D;
   static constexpr int NB = GOPS ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
   static constexpr int TPE = VS ? L * NV : L;
@@ -528,7 +532,7 @@ struct StageGeom {
 // EXACT: the exact-mass variant (face terms lifted by M^-1 e_0 / M^-1 e_N onto every node).
 template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
-  using G = StageGeom<DIM, N, EQ, real, VS>;
+  using G = StageGeom<DIM, N, EQ, real, VS, FF>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
   constexpr bool EARLY = DIM <= 2 && !FF;
   // BPF (FP32, elements a multiple of 16 bytes; Euler or the bulk-copy layouts): the update's
@@ -1068,16 +1072,25 @@ __global__ void __maxnreg__(96) stage_kernel_r96(const StageArgs<real> args) {
   if constexpr (use_euler3d_f32<DIM, N, EQ, real, VS, FF, EXACT>()) euler3d_f32_body<N>(args);
   else stage_body<DIM, N, EQ, real, VS, FF, EXACT>(args);
 }
+// Float-float 3D Euler, degree 5, one thread per line (StageGeom::FF3D): registers capped at
+// 168 (uncapped the compiler takes 240; 136-168 measured alike, below 152 with spills).
+constexpr int FF3D_REGS = 168;
+template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
+__global__ void __maxnreg__(FF3D_REGS) stage_kernel_ff3d(const StageArgs<real> args) {
+  stage_body<DIM, N, EQ, real, VS, FF, EXACT>(args);
+}
 // The entry point of a kernel class.
 template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 constexpr auto stage_entry() {
-  if constexpr (DIM == 3 && sizeof(real) == 4) return &stage_kernel_r96<DIM, N, EQ, real, VS, FF, EXACT>;
+  if constexpr (StageGeom<DIM, N, EQ, real, VS, FF>::FF3D && !EXACT)
+    return &stage_kernel_ff3d<DIM, N, EQ, real, VS, FF, EXACT>;
+  else if constexpr (DIM == 3 && sizeof(real) == 4) return &stage_kernel_r96<DIM, N, EQ, real, VS, FF, EXACT>;
   else return &stage_kernel<DIM, N, EQ, real, VS, FF, EXACT>;
 }
 
 template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 void stage_shape(int epb, int* threads, size_t* smem) {
-  using G = StageGeom<DIM, N, EQ, real, VS>;
+  using G = StageGeom<DIM, N, EQ, real, VS, FF>;
   *threads = epb * G::TPE;
   if constexpr (use_euler3d_f32<DIM, N, EQ, real, VS, FF, EXACT>()) {
     *smem = euler3d_f32_smem<N>(epb);

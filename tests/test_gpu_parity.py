@@ -261,6 +261,8 @@ def test_config4_full_size_sampled_rk4_rk6():
     dt = orc.stable_dt(p, U0, 0.1)
     _patch_check(3, 5, (64, 64, 64), 1, U0, dt, 4, [(0, 0, 0), (63, 31, 5), (10, 63, 63)])
     _patch_check(3, 5, (64, 64, 64), 1, U0, dt, 6, [(0, 63, 0), (33, 2, 40)])
+    # the float-float contraction at the FP64 bar (its own register-capped kernel at this degree)
+    _patch_check(3, 5, (64, 64, 64), 1, U0, dt, 4, [(0, 0, 0), (40, 63, 17)], dtype="f64ff")
 
 
 def test_norms_match_oracle():
@@ -445,12 +447,24 @@ def test_float_float_contraction_2d(N, eq):
 
 
 @pytest.mark.parametrize("dim,N,E,eq,rk", [(1, 3, (9,), 0, 4), (1, 6, (7,), 1, 6), (3, 2, (3, 2, 3), 1, 4),
-                                           (3, 5, (2, 3, 2), 0, 3), (3, 3, (2, 2, 3), 1, 6), (2, 7, (4, 3), 1, 6)])
+                                           (3, 5, (2, 3, 2), 0, 3), (3, 3, (2, 2, 3), 1, 6), (2, 7, (4, 3), 1, 6),
+                                           (3, 5, (3, 2, 3), 1, 3), (3, 5, (2, 3, 2), 1, 4), (3, 5, (2, 2, 3), 1, 6),
+                                           (3, 7, (2, 2, 3), 1, 4)])
 def test_float_float_contraction_1d_3d_rk(dim, N, E, eq, rk):
     p, s = make(dim, N, E, eq, dtype="f64ff", epb=3, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3))
     U = initial(p)
     dt = orc.stable_dt(p, U, 0.2)
     check(p, s, U, dt, 3, rk, F64_TOL)
+    if dim == 3 and eq == 1:
+        # tiles of 1, 2, 4 (ragged) and 3 elements give the same bits
+        outs = []
+        for epb in (1, 2, 3, 4):
+            _, t = make(dim, N, E, eq, dtype="f64ff", epb=epb, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3))
+            t.set_state(U)
+            t.step(dt, 2, rk)
+            outs.append(t.get_state())
+            t.close()
+        assert all(np.array_equal(o, outs[0]) for o in outs[1:])
 
 
 def test_float_float_falls_back_to_fp64_for_unsplittable_values():
