@@ -18,10 +18,15 @@
 //   - the solve's fields (pointers, scales, RK coefficients) live in shared memory, not in
 //     registers, which the line work needs under the 96-register cap (0.939 / 0.232).
 // Measured slower and left out: the update's U^n / ACC copied into shared memory by bulk copies,
-// a second stage-input slot with the next tile's copy in flight, the next tile's copy issued
-// before the update, the neighbour traces staged in shared memory by cp.async, neighbour traces
-// inside the tile read from shared memory, register caps of 72 and 80 (spills), and two threads
-// per line (one per variable pair).
+// a second stage-input slot with the next tile's copy in flight (issued right after the current
+// tile's wait: 64^3 0.933 -> 1.066 ms, 32^3 degree 7 0.227 -> 0.305 ms), the next tile's copy
+// issued before the update, both quads of a thread's update loaded before either is stored (the
+// loads need 64 registers: spills under the cap, 0.933 -> 1.107 ms), the neighbour traces staged
+// in shared memory by cp.async, neighbour traces inside the tile read from shared memory, register
+// caps of 72 and 80 (spills), and two threads per line (one per variable pair).
+// Phase profile at 64^3 (clock64 at one thread per CTA, all four RK4 stages, cycles per tile of
+// four elements): copy wait 3.1k, axis 0 2.2k, axis 1 3.1k, axis 2 3.4k, update 4.1k; with four
+// CTAs per SM in these phases the SM issues about half of the cycles.
 // The tile arrives as before by bulk copies on an mbarrier (one per element and variable at
 // degree 5: 864 contiguous bytes; one per 256-byte z-plane at degree 7), with the same bounded
 // wait, failure flag and test switch.
