@@ -474,7 +474,7 @@ def run_workload_table(dev, peaks, names):
         del X
         row = {"workload": desc, "dof": ndof_of(dim, deg, el, eq)}
         finals = {}
-        for dtype in (("f64", "f32", "f64ff") if name in ("adv2d", "euler3d") else ("f64", "f32")):
+        for dtype in ("f64", "f32", "f64ff"):
             r, final, n, dt = timed_row(name, dtype, dev, peaks, U0)
             row[dtype] = r
             log(f"{name} {dtype}: {r['ms_per_stage']:.4f} ms per stage ({n} RK4 steps)")

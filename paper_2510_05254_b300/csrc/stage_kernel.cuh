@@ -760,6 +760,13 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
     // ---- 3. volume + surface terms, axis by axis (FUSED: the last axis applies the stage update
     //         to the finished right-hand side of its line directly) ----
     const ElemXYZ exyz_t = elem_xyz((unsigned)(e0 + el_t), S.E0, S.E1);  // this thread's element
+    // Float-float Euler with one thread per line: the variable loop stays a loop (unrolled, its
+    // four float-float contractions made a body that missed the instruction cache).  Measured per
+    // RK4 stage: 3D degree 5 at 64^3 14.91 -> 12.59 ms, 3D degree 7 at 32^3 4.53 -> 3.74 ms, 2D
+    // degree 7 at 512^2 2.42 -> 2.10 ms (FP64: 16.10, 4.33, 2.28); the plain FP64 kernel keeps it
+    // unrolled (3D degree 5: 16.10 -> 16.77 rolled).  The operations and their order are the same.
+    constexpr bool ROLLV = FF && EQ == 1 && !VS && ((DIM == 3 && (N == 5 || N == 7)) || (DIM == 2 && N == 7));
+    constexpr int UNR_V = ROLLV ? 1 : NV;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const bool last = FUSED && a == DIM - 1;
@@ -907,7 +914,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
           const real unhi = ratio(xhi[1 + a], xhi[0]);
           const real alo = fmax(fabs(unlo), fabs(un0)) + cs;
           const real ahi = fmax(fabs(unN), fabs(unhi)) + cs;
-#pragma unroll
+#pragma unroll UNR_V
           for (int v = 0; v < NV; ++v) {
             if (VS && v != vsel) continue;
             const real* sUv = sUe + v * epb * SPE;
