@@ -766,7 +766,11 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
     // degree 7 at 512^2 2.42 -> 2.10 ms (FP64: 16.10, 4.33, 2.28); the plain FP64 kernel keeps it
     // unrolled (3D degree 5: 16.10 -> 16.77 rolled).  The operations and their order are the same.
     constexpr bool ROLLV = FF && EQ == 1 && !VS && ((DIM == 3 && (N == 5 || N == 7)) || (DIM == 2 && N == 7));
-    constexpr int UNR_V = ROLLV ? 1 : NV;
+    // the variable loop's trip count, hidden from the compiler where the loop stays rolled (a
+    // bare unroll pragma unrolls only loops of known trip count; a count on the pragma changed
+    // the code, and the registers, of the other kernels too)
+    int nv_loop = NV;
+    if constexpr (ROLLV) asm volatile("" : "+r"(nv_loop));
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const bool last = FUSED && a == DIM - 1;
@@ -914,8 +918,8 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
           const real unhi = ratio(xhi[1 + a], xhi[0]);
           const real alo = fmax(fabs(unlo), fabs(un0)) + cs;
           const real ahi = fmax(fabs(unN), fabs(unhi)) + cs;
-#pragma unroll UNR_V
-          for (int v = 0; v < NV; ++v) {
+#pragma unroll
+          for (int v = 0; v < nv_loop; ++v) {
             if (VS && v != vsel) continue;
             const real* sUv = sUe + v * epb * SPE;
             real bb[n], aa[n];
