@@ -21,7 +21,9 @@
 // a second stage-input slot with the next tile's copy in flight (issued right after the current
 // tile's wait: 64^3 0.933 -> 1.066 ms, 32^3 degree 7 0.227 -> 0.305 ms), the next tile's copy
 // issued before the update, both quads of a thread's update loaded before either is stored (the
-// loads need 64 registers: spills under the cap, 0.933 -> 1.107 ms), the neighbour traces staged
+// loads need 64 registers: spills under the cap, 0.933 -> 1.107 ms), ACC alone copied into shared
+// memory with the tile on its own barrier and U^n of both quads loaded first (no spills, four
+// CTAs per SM still: 0.933 -> 0.982 ms), the neighbour traces staged
 // in shared memory by cp.async, neighbour traces inside the tile read from shared memory, register
 // caps of 72 and 80 (spills), and two threads per line (one per variable pair).
 // Phase profile at 64^3 (clock64 at one thread per CTA, all four RK4 stages, cycles per tile of
