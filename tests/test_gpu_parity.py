@@ -314,8 +314,11 @@ def test_device_state_round_trip_and_node_coords():
 
 
 def test_batch_is_bitwise_identical_to_individual_solves():
+    # two solves share a launch where their classes match (the float-float 3D degree-5 and 2D
+    # degree-7 Euler classes included)
     specs = [(2, 7, (6, 5), 0, "f64"), (2, 3, (9, 4), 1, "f64"), (2, 7, (3, 3), 0, "f64"),
-             (2, 5, (4, 4), 1, "f32"), (3, 2, (2, 3, 2), 1, "f64")]
+             (2, 5, (4, 4), 1, "f32"), (3, 2, (2, 3, 2), 1, "f64"), (3, 5, (2, 3, 2), 1, "f64ff"),
+             (3, 5, (3, 2, 2), 1, "f64ff"), (2, 7, (3, 4), 1, "f64ff")]
     alone, batched, states, dts = [], [], [], []
     for dim, N, E, eq, dt_ in specs:
         p, s = make(dim, N, E, eq, dtype=dt_)

@@ -1,6 +1,7 @@
 """Domain decomposition with a face-trace halo exchange (ndg_partition_*), emulated on one GPU:
 the partitioned solve must equal the unpartitioned one bit for bit (same per-element arithmetic;
-only where the neighbour's trace is read from changes), for uneven splits in 1D/2D/3D."""
+only where the neighbour's trace is read from changes), for uneven splits in 1D/2D/3D, in FP64,
+FP32 and with the float-float contraction (its own kernels for 3D Euler at degrees 5 and 7)."""
 import numpy as np
 import pytest
 
@@ -30,17 +31,17 @@ def _cfg(dim, N, E, eq, dtype):
         cfg.length[a] = (1.0, 0.8, 1.2)[a]
     cfg.velocity[0], cfg.velocity[1], cfg.velocity[2] = 0.7, -0.4, 0.3
     cfg.equation, cfg.flux = eq, (0 if eq == 0 else 1)
-    cfg.dtype = nat.NDG_F64 if dtype == "f64" else nat.NDG_F32
+    cfg.dtype = {"f64": nat.NDG_F64, "f32": nat.NDG_F32, "f64ff": nat.NDG_F64_FF}[dtype]
     return cfg
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f64ff"])
 @pytest.mark.parametrize("rk", [4, 6])
 @pytest.mark.parametrize("dim,N,E,eq,parts", CASES)
 def test_partitioned_equals_unpartitioned(dim, N, E, eq, parts, rk, dtype):
     p = orc.Problem(dim=dim, degree=N, elems=E + (1,) * (3 - dim), equation=eq, flux=0 if eq == 0 else 1,
                     length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3))
-    U = initial(p).astype(np.float64 if dtype == "f64" else np.float32)
+    U = initial(p).astype(np.float32 if dtype == "f32" else np.float64)
     dt = orc.stable_dt(p, U.astype(np.float64), 0.2)
     s = Solver(dim, N, E, equation=eq, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3), dtype=dtype)
     s.set_state(U)
