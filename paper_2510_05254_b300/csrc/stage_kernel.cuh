@@ -762,10 +762,13 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
     const ElemXYZ exyz_t = elem_xyz((unsigned)(e0 + el_t), S.E0, S.E1);  // this thread's element
     // Float-float Euler with one thread per line: the variable loop stays a loop (unrolled, its
     // four float-float contractions made a body that missed the instruction cache).  Measured per
-    // RK4 stage: 3D degree 5 at 64^3 14.91 -> 12.59 ms, 3D degree 7 at 32^3 4.53 -> 3.74 ms, 2D
-    // degree 7 at 512^2 2.42 -> 2.10 ms (FP64: 16.10, 4.33, 2.28); the plain FP64 kernel keeps it
-    // unrolled (3D degree 5: 16.10 -> 16.77 rolled).  The operations and their order are the same.
-    constexpr bool ROLLV = FF && EQ == 1 && !VS && ((DIM == 3 && (N == 5 || N == 7)) || (DIM == 2 && N == 7));
+    // RK4 stage, unrolled -> rolled (plain FP64 beside): 3D degree 3 at 96^3 12.95 -> 11.94 ms
+    // (14.02), degree 4 at 72^3 14.90 -> 12.38 (13.61), degree 5 at 64^3 14.91 -> 12.59 (16.10),
+    // degree 6 at 40^3 7.27 -> 5.88 (6.90), degree 7 at 32^3 4.53 -> 3.74 (4.33); 2D degree 6 at
+    // 420^2 1.20 -> 1.11 (1.24), degree 7 at 512^2 2.42 -> 2.10 (2.28); 2D degrees 4 and 5 alike
+    // or slower rolled, so they stay unrolled, as does the plain FP64 kernel (3D degree 5: 16.10 ->
+    // 16.77 rolled).  The operations and their order are the same.
+    constexpr bool ROLLV = FF && EQ == 1 && !VS && ((DIM == 3 && N >= 3) || (DIM == 2 && N >= 6));
     // the variable loop's trip count, hidden from the compiler where the loop stays rolled (a
     // bare unroll pragma unrolls only loops of known trip count; a count on the pragma changed
     // the code, and the registers, of the other kernels too)
