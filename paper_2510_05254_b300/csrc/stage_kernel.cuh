@@ -500,11 +500,13 @@ struct StageGeom {
   // and with them half the CTAs an SM holds (measured: 32^3 FP64 5.16 -> 4.36 ms per stage; at
   // degree 5, where registers bind first, 16.07 -> 16.19, so it keeps them).  The
   // line-and-variable mapping keeps them too: the global loads cost registers its large CTAs do
-  // not have.  Float-float 3D Euler at degree 5 with one thread per line: with its registers
-  // capped at 168 (FF3D_REGS) shared memory binds, and without the staged copies three CTAs of
-  // three elements fit an SM instead of one of six (measured at 64^3: 17.07 -> 14.91 ms per
-  // stage; FP64 16.10).  At degree 7 and in 2D the same changes measured slower.
-  static constexpr bool FF3D = FF && DIM == 3 && EQ == 1 && N == 5 && !VS;
+  // not have.  Float-float 3D Euler at degrees 4-6 with one thread per line: with its registers
+  // capped at 168 (FF3D_REGS) shared memory binds, and without the staged copies more CTAs fit an
+  // SM (degree 5 at 64^3: three CTAs of three elements instead of one of six, 17.07 -> 14.91 ms
+  // per stage unrolled; with the rolled variable loop, degree 4 at 72^3 12.37 -> 10.29 ms, degree
+  // 6 at 40^3 5.87 -> 4.87 ms).  At degree 7 (3.76 -> 3.96 ms) and in 2D the same changes
+  // measured slower.
+  static constexpr bool FF3D = FF && DIM == 3 && EQ == 1 && N >= 4 && N <= 6 && !VS;
   static constexpr bool GOPS = SLIM || (DIM == 3 && !VS && N == 7) || FF3D;
   static constexpr int NB = GOPS ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
@@ -1086,8 +1088,9 @@ __global__ void __maxnreg__(96) stage_kernel_r96(const StageArgs<real> args) {
   if constexpr (use_euler3d_f32<DIM, N, EQ, real, VS, FF, EXACT>()) euler3d_f32_body<N>(args);
   else stage_body<DIM, N, EQ, real, VS, FF, EXACT>(args);
 }
-// Float-float 3D Euler, degree 5, one thread per line (StageGeom::FF3D): registers capped at
-// 168 (uncapped the compiler takes 240; 136-168 measured alike, below 152 with spills).
+// Float-float 3D Euler, degrees 4-6, one thread per line (StageGeom::FF3D): registers capped at
+// 168 (uncapped the compiler takes 208-240; at degree 5 caps of 136-168 measured alike, below 152
+// with spills).
 constexpr int FF3D_REGS = 168;
 template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool EXACT = false>
 __global__ void __maxnreg__(FF3D_REGS) stage_kernel_ff3d(const StageArgs<real> args) {
