@@ -500,13 +500,13 @@ struct StageGeom {
   // and with them half the CTAs an SM holds (measured: 32^3 FP64 5.16 -> 4.36 ms per stage; at
   // degree 5, where registers bind first, 16.07 -> 16.19, so it keeps them).  The
   // line-and-variable mapping keeps them too: the global loads cost registers its large CTAs do
-  // not have.  Float-float 3D Euler at degrees 4-6 with one thread per line: with its registers
+  // not have.  Float-float 3D Euler at degrees 3-6 with one thread per line: with its registers
   // capped at 168 (FF3D_REGS) shared memory binds, and without the staged copies more CTAs fit an
   // SM (degree 5 at 64^3: three CTAs of three elements instead of one of six, 17.07 -> 14.91 ms
-  // per stage unrolled; with the rolled variable loop, degree 4 at 72^3 12.37 -> 10.29 ms, degree
-  // 6 at 40^3 5.87 -> 4.87 ms).  At degree 7 (3.76 -> 3.96 ms) and in 2D the same changes
-  // measured slower.
-  static constexpr bool FF3D = FF && DIM == 3 && EQ == 1 && N >= 4 && N <= 6 && !VS;
+  // per stage unrolled; with the rolled variable loop, degree 3 at 96^3 11.91 -> 11.22 ms, degree
+  // 4 at 72^3 12.37 -> 10.29 ms, degree 6 at 40^3 5.87 -> 4.87 ms).  At degrees 2 (14.19 ->
+  // 14.80 ms at 128^3) and 7 (3.76 -> 3.96 ms) and in 2D the same changes measured slower.
+  static constexpr bool FF3D = FF && DIM == 3 && EQ == 1 && N >= 3 && N <= 6 && !VS;
   static constexpr bool GOPS = SLIM || (DIM == 3 && !VS && N == 7) || FF3D;
   static constexpr int NB = GOPS ? 0 : 2 * NV;  // unpadded shared arrays of NPE per element: U^n and ACC
   // threads per element: one per line, or (VS) one per line and variable
@@ -1088,7 +1088,7 @@ __global__ void __maxnreg__(96) stage_kernel_r96(const StageArgs<real> args) {
   if constexpr (use_euler3d_f32<DIM, N, EQ, real, VS, FF, EXACT>()) euler3d_f32_body<N>(args);
   else stage_body<DIM, N, EQ, real, VS, FF, EXACT>(args);
 }
-// Float-float 3D Euler, degrees 4-6, one thread per line (StageGeom::FF3D): registers capped at
+// Float-float 3D Euler, degrees 3-6, one thread per line (StageGeom::FF3D): registers capped at
 // 168 (uncapped the compiler takes 208-240; at degree 5 caps of 136-168 measured alike, below 152
 // with spills).
 constexpr int FF3D_REGS = 168;

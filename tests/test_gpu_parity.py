@@ -452,7 +452,8 @@ def test_float_float_contraction_2d(N, eq):
 @pytest.mark.parametrize("dim,N,E,eq,rk", [(1, 3, (9,), 0, 4), (1, 6, (7,), 1, 6), (3, 2, (3, 2, 3), 1, 4),
                                            (3, 5, (2, 3, 2), 0, 3), (3, 3, (2, 2, 3), 1, 6), (2, 7, (4, 3), 1, 6),
                                            (3, 5, (3, 2, 3), 1, 3), (3, 5, (2, 3, 2), 1, 4), (3, 5, (2, 2, 3), 1, 6),
-                                           (3, 7, (2, 2, 3), 1, 4), (3, 4, (2, 3, 2), 1, 4), (3, 6, (2, 2, 3), 1, 6)])
+                                           (3, 7, (2, 2, 3), 1, 4), (3, 4, (2, 3, 2), 1, 4), (3, 6, (2, 2, 3), 1, 6),
+                                           (3, 3, (3, 2, 2), 1, 3)])
 def test_float_float_contraction_1d_3d_rk(dim, N, E, eq, rk):
     p, s = make(dim, N, E, eq, dtype="f64ff", epb=3, length=(1.0, 0.8, 1.2), velocity=(0.7, -0.4, 0.3))
     U = initial(p)
