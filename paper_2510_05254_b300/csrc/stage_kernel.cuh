@@ -536,7 +536,11 @@ template <int DIM, int N, int EQ, typename real, bool VS, bool FF = false, bool 
 __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   using G = StageGeom<DIM, N, EQ, real, VS, FF>;
   constexpr int n = G::n, L = G::L, NPE = G::NPE, NV = G::NV, SPE = G::SPE, TPE = G::TPE;
-  constexpr bool EARLY = DIM <= 2 && !FF;
+  // float-float 2D Euler at degrees 6-7 (its variable loop rolled, see ROLLV): EARLY and FUSED
+  // below pay there too (512^2 degree 7 2.13 -> 1.89 ms per stage, 420^2 degree 6 1.11 -> 1.05;
+  // EARLY alone 2.07 / 1.15, FUSED alone 2.13 / 1.11)
+  constexpr bool FF2E = FF && DIM == 2 && EQ == 1 && N >= 6 && !VS;
+  constexpr bool EARLY = DIM <= 2 && (!FF || FF2E);
   // BPF (FP32, elements a multiple of 16 bytes; Euler or the bulk-copy layouts): the update's
   // U^n / ACC reach L2 by bulk prefetches (16-byte aligned ranges: the arrays are 256-byte
   // aligned).  Measured on the 16-byte 2D layouts: Euler degree 7 170 -> 167 us, advection
@@ -547,7 +551,7 @@ __device__ __forceinline__ void stage_body(const StageArgs<real>& args) {
   // stage).  Elsewhere the extra registers cost more occupancy than the round trip does (measured:
   // FP32 2D Euler 243 -> 260 us, float-float 93 -> 95 us, FP64 3D Euler no gain), so those keep the
   // node-parallel update.
-  constexpr bool FUSED = DIM == 2 && !G::SLIM && !FF;
+  constexpr bool FUSED = DIM == 2 && !G::SLIM && (!FF || FF2E);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const GroupHeader hdr = *args.hdr;
   const int epb = hdr.epb;
