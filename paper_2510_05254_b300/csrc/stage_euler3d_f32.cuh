@@ -138,11 +138,51 @@ struct SolveShared {
   float c, c2, a_self, bdt, dts;
 };
 
+// Stored slopes (RK6): the stage combination of four nodes, W variables at a time (the slopes'
+// float4 loads of those variables issued together; node by node, with 4-byte loads between the
+// stores, they were serialised: 64^3 RK6 2.19 -> 1.36 ms per stage).  Per node the operations and
+// their order are stage_update_node's.
+template <int SPE, int W>
+__device__ __forceinline__ void stage_update_slopes4(const StageArgs<float>& args, const SolveShared& ss, int si,
+                                                     const StagePlan& plan, long long g, long long vstride,
+                                                     const float* sr, const float4 (&a)[4], const float4 (&b)[4]) {
+  float* acc = ss.acc;
+  float* uout = ss.uout;
+  float* kw = ss.kw;
+  const float a_self = ss.a_self, bdt = ss.bdt;
+#pragma unroll
+  for (int p = 0; p < 4; p += W) {
+    float4 r[W], o[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      r[q] = *reinterpret_cast<const float4*>(sr + (p + q) * SPE);
+      o[q] = fma4(a_self, r[q], b[p + q]);
+    }
+    for (int j = 0; j < plan.nread; ++j) {
+      const float* kj = static_cast<const float*>(args.solves[si].buf[plan.kread[j]]);
+      const float aj = plan.a_read_f[j] * ss.dts;
+      float4 kv[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) kv[q] = __ldg(reinterpret_cast<const float4*>(kj + (p + q) * vstride + g));
+#pragma unroll
+      for (int q = 0; q < W; ++q) o[q] = fma4(aj, kv[q], o[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const long long gv = (p + q) * vstride + g;
+      *reinterpret_cast<float4*>(uout + gv) = o[q];
+      if (plan.acc_mode == 1) *reinterpret_cast<float4*>(acc + gv) = fma4(bdt, r[q], b[p + q]);
+      else if (plan.acc_mode == 2) *reinterpret_cast<float4*>(acc + gv) = fma4(bdt, r[q], a[p + q]);
+      if (kw) *reinterpret_cast<float4*>(kw + gv) = r[q];
+    }
+  }
+}
+
 // The update of one quad of all four variables: every global load of the four variables is issued
 // before the first store, so their latencies overlap (variable by variable, a store might alias
 // the next variable's loads as far as the compiler knows, which would serialise them).  The
 // arithmetic per node is stage_update_quad's (stage_update_node's with stored slopes, RK6).
-template <int SPE>
+template <int SPE, int SW>
 __device__ __forceinline__ void stage_update_quads4(const StageArgs<float>& args, const SolveShared& ss, int si,
                                                     const StagePlan& plan, long long g, long long vstride,
                                                     const float* sr, const float* su) {
@@ -161,28 +201,14 @@ __device__ __forceinline__ void stage_update_quads4(const StageArgs<float>& args
       b[v] = plan.in == kUN ? *reinterpret_cast<const float4*>(su + v * SPE)
                             : __ldg(reinterpret_cast<const float4*>(un + v * vstride + g));
   }
+  if (plan.nread > 0) {
+    stage_update_slopes4<SPE, SW>(args, ss, si, plan, g, vstride, sr, a, b);
+    return;
+  }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const float4 r = *reinterpret_cast<const float4*>(sr + v * SPE);
     const long long gv = v * vstride + g;
-    if (plan.nread > 0) {
-      // stored slopes (RK6): node by node, as stage_update_node
-      const float rr[4] = {r.x, r.y, r.z, r.w}, bb[4] = {b[v].x, b[v].y, b[v].z, b[v].w},
-                  aa[4] = {a[v].x, a[v].y, a[v].z, a[v].w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float o = fmaf(a_self, rr[k], bb[k]);
-        for (int j = 0; j < plan.nread; ++j) {
-          const float* kj = static_cast<const float*>(args.solves[si].buf[plan.kread[j]]);
-          o = fmaf(plan.a_read_f[j] * ss.dts, kj[gv + k], o);
-        }
-        uout[gv + k] = o;
-        if (plan.acc_mode == 1) acc[gv + k] = fmaf(bdt, rr[k], bb[k]);
-        else if (plan.acc_mode == 2) acc[gv + k] = fmaf(bdt, rr[k], aa[k]);
-        if (kw) kw[gv + k] = rr[k];
-      }
-      continue;
-    }
     const float2 rl = make_float2(r.x, r.y), rh = make_float2(r.z, r.w);
     const float2 al = make_float2(a[v].x, a[v].y), ah = make_float2(a[v].z, a[v].w);
     const float2 bl = make_float2(b[v].x, b[v].y), bh = make_float2(b[v].z, b[v].w);
@@ -388,12 +414,17 @@ __device__ __forceinline__ void euler3d_f32_body(const StageArgs<float>& args) {
     }
 
     // ---- 3. Runge-Kutta stage update: four consecutive nodes of every variable per step ----
+    // stored slopes (RK6) two variables at a time at degree 5, one at degree 7, where wider
+    // batches cost the RK4 stages registers (RK4 / RK6 ms per stage, widths 1, 2, 4: degree 5 at
+    // 64^3 0.930 / 1.630, 0.914 / 1.364, 0.915 / 1.350; degree 7 at 32^3 0.2327 / 0.387, 0.2361 /
+    // 0.375, 0.2613 / 0.415)
+    constexpr int SLOPE_W = N == 7 ? 1 : 2;
     const int quads = cnt * NPE / 4;
     for (int q = tid; q < quads; q += nthr) {
       const int el = q / (NPE / 4);
       const int node = 4 * (q - el * (NPE / 4));
       const int sl = el * ES + G::pad(node);
-      stage_update_quads4<SPE>(args, *sS, si, plan, e0 * NPE + 4 * q, vstride, sR + sl, sU + sl);
+      stage_update_quads4<SPE, SLOPE_W>(args, *sS, si, plan, e0 * NPE + 4 * q, vstride, sR + sl, sU + sl);
     }
     __syncthreads();
   }

@@ -278,6 +278,11 @@ __device__ __forceinline__ void stage_update_node(const StageArgs<real>& args, c
   if (S.kw) S.kw[g] = r;
 }
 
+// s x + y lane by lane (four FMAs, each rounded as the scalar one)
+__device__ __forceinline__ float4 fma4(float s, float4 x, float4 y) {
+  return make_float4(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y), fmaf(s, x.z, y.z), fmaf(s, x.w, y.w));
+}
+
 // The update of four consecutive nodes g .. g + 3 (16-byte aligned in every array), FP32: r and
 // the stage input (U^n at the first stage) read as float4 from shared memory, U^n / ACC as float4
 // from global memory; the same arithmetic as stage_update_node, node by node.
@@ -294,10 +299,18 @@ __device__ __forceinline__ void stage_update_quad(const StageArgs<float>& args, 
         make_float4(fmaf(S.bdt, r.x, a.x), fmaf(S.bdt, r.y, a.y), fmaf(S.bdt, r.z, a.z), fmaf(S.bdt, r.w, a.w));
     return;
   }
-  if (plan.nread > 0) {  // stored slopes (RK6): node by node
-    const float rr[4] = {r.x, r.y, r.z, r.w}, bb[4] = {b.x, b.y, b.z, b.w}, aa[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) stage_update_node(args, S, si, plan, g + k, rr[k], bb[k], aa[k]);
+  if (plan.nread > 0) {
+    // stored slopes (RK6): the four nodes at once, one float4 load per slope; per node the
+    // operations and their order are stage_update_node's
+    float4 o = fma4(S.a_self, r, b);
+    for (int j = 0; j < plan.nread; ++j) {
+      const float* kj = static_cast<const float*>(args.solves[si].buf[plan.kread[j]]);
+      o = fma4(S.a_read(plan, j), __ldg(reinterpret_cast<const float4*>(kj + g)), o);
+    }
+    *reinterpret_cast<float4*>(S.uout + g) = o;
+    if (plan.acc_mode == 1) *reinterpret_cast<float4*>(S.acc + g) = fma4(S.bdt, r, b);
+    else if (plan.acc_mode == 2) *reinterpret_cast<float4*>(S.acc + g) = fma4(S.bdt, r, a);
+    if (S.kw) *reinterpret_cast<float4*>(S.kw + g) = r;
     return;
   }
   *reinterpret_cast<float4*>(S.uout + g) =
