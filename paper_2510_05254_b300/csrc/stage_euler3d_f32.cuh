@@ -25,7 +25,12 @@
 // memory with the tile on its own barrier and U^n of both quads loaded first (no spills, four
 // CTAs per SM still: 0.933 -> 0.982 ms), the neighbour traces staged
 // in shared memory by cp.async, neighbour traces inside the tile read from shared memory, register
-// caps of 72 and 80 (spills), and two threads per line (one per variable pair).
+// caps of 72 and 80 (spills), and two threads per line (one per variable pair).  Also measured
+// slower at 64^3 degree 5 (ms per RK4 stage against 0.914-0.917 in the same runs): the stage input
+// of the tiles across the upper y and z faces prefetched into L2 by bulk prefetches with the tile
+// (0.983; upper z only: 0.979), and an update balanced over the CTA's threads -- each thread one
+// x-line of six nodes (1.118: its float2 accesses are 24 bytes apart across a warp) or three
+// float2 stripes per variable, consecutive across the warp (1.015, spilling under the cap).
 // Phase profile at 64^3 (clock64 at one thread per CTA, all four RK4 stages, cycles per tile of
 // four elements): copy wait 3.1k, axis 0 2.2k, axis 1 3.1k, axis 2 3.4k, update 4.1k; with four
 // CTAs per SM in these phases the SM issues about half of the cycles.
@@ -40,6 +45,23 @@ namespace ndg {
 // lane equals the scalar subtraction (signed zeros included)
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+
+// Loads of data that a tile reads once (U^n, ACC and stored slopes in the stage update).  At
+// degree 7 they take the non-coherent path without allocating in L1, which keeps L1 for the
+// neighbour traces (32^3: 0.2340 -> 0.2299 ms per RK4 stage); at degree 5 that measured slower
+// (64^3: 0.9129 -> 0.9204 ms), so those stay plain read-only loads.
+template <bool NA>
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  if constexpr (NA) {
+    float4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(p));
+    return r;
+  } else {
+    return __ldg(p);
+  }
+}
 
 template <int N>
 struct Euler3dF32Geom {
@@ -60,6 +82,10 @@ struct Euler3dF32Geom {
   static constexpr int XW = PLANE ? 4 : 2;  // x-line access width (floats)
   __device__ static __forceinline__ int pad(int node) { return PLANE ? node + 8 * (node / (n * n)) : node; }
 };
+
+// the update's loads are non-allocating for the degree-7 class (its SPE) only
+template <int SPE>
+constexpr bool kDeg7 = SPE == Euler3dF32Geom<7>::SPE;
 
 // D along one line for two variables at once (the even-odd halves of contract_even_odd, even n).
 template <int N>
@@ -163,7 +189,8 @@ __device__ __forceinline__ void stage_update_slopes4(const StageArgs<float>& arg
       const float aj = plan.a_read_f[j] * ss.dts;
       float4 kv[W];
 #pragma unroll
-      for (int q = 0; q < W; ++q) kv[q] = __ldg(reinterpret_cast<const float4*>(kj + (p + q) * vstride + g));
+      for (int q = 0; q < W; ++q)
+        kv[q] = ld_stream<kDeg7<SPE>>(reinterpret_cast<const float4*>(kj + (p + q) * vstride + g));
 #pragma unroll
       for (int q = 0; q < W; ++q) o[q] = fma4(aj, kv[q], o[q]);
     }
@@ -196,10 +223,10 @@ __device__ __forceinline__ void stage_update_quads4(const StageArgs<float>& args
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     a[v] = b[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (plan.acc_mode >= 2) a[v] = __ldg(reinterpret_cast<const float4*>(acc + v * vstride + g));
+    if (plan.acc_mode >= 2) a[v] = ld_stream<kDeg7<SPE>>(reinterpret_cast<const float4*>(acc + v * vstride + g));
     if (plan.acc_mode != 3)
       b[v] = plan.in == kUN ? *reinterpret_cast<const float4*>(su + v * SPE)
-                            : __ldg(reinterpret_cast<const float4*>(un + v * vstride + g));
+                            : ld_stream<kDeg7<SPE>>(reinterpret_cast<const float4*>(un + v * vstride + g));
   }
   if (plan.nread > 0) {
     stage_update_slopes4<SPE, SW>(args, ss, si, plan, g, vstride, sr, a, b);
