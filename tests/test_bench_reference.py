@@ -44,3 +44,17 @@ def test_traffic_is_reported_only_for_the_captured_kernel_sources(monkeypatch):
     assert bench.traffic_per_launch("adv2d", "f64", False) is None
     monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA1", "0" * 40)
     assert bench.traffic_per_launch("euler3d", "f32", False) is None
+
+
+def test_committed_traffic_capture_is_of_the_committed_kernel_sources():
+    """The DRAM traffic figures in bench.py were captured from the kernel sources as committed
+    (their code digest), and the profile summary that records the capture names the same digest
+    and the same per-launch figures; a kernel change without a new capture fails here."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.kernel_sources_sha1() == bench.TRAFFIC_SOURCES_SHA1
+    summary = open(os.path.join(ROOT, "profiles", "stage_kernel_euler3d_deg5_64cubed.md")).read()
+    assert bench.TRAFFIC_SOURCES_SHA1 in summary
+    for dtype in ("f64", "f32"):
+        figure = ("(%.4e)" % bench.TRAFFIC_PER_LAUNCH[("euler3d", dtype)]).replace("e+09", "e9")
+        assert figure in summary
