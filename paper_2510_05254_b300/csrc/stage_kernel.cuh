@@ -511,7 +511,9 @@ struct StageGeom {
   // tile) instead of copies staged in shared memory.  FP32 always; FP64 in 3D at degree 7 with one
   // thread per line, where the staged copies take 32 of an Euler element's 84 KB of shared memory
   // and with them half the CTAs an SM holds (measured: 32^3 FP64 5.16 -> 4.36 ms per stage; at
-  // degree 5, where registers bind first, 16.07 -> 16.19, so it keeps them).  The
+  // degree 5, where registers bind first, 16.07 -> 16.19, so it keeps them; also with the entry's
+  // registers capped at 168 (152 used, no spills) and tiles of 2, 3, 4, 6 or 8 elements, up to
+  // three CTAs per SM: 18.44, 16.55, 16.17, 16.57, 15.91 ms against 16.07 staged -- 1 % at best).  The
   // line-and-variable mapping keeps them too: the global loads cost registers its large CTAs do
   // not have.  Float-float 3D Euler at degrees 3-6 with one thread per line: with its registers
   // capped at 168 (FF3D_REGS) shared memory binds, and without the staged copies more CTAs fit an
