@@ -34,6 +34,8 @@
 // the update fused into the z pass, each z-line thread updating its own six nodes from registers
 // (no right-hand-side round trip, one barrier less; coalesced 4-byte accesses: 1.190 with the
 // loads node by node, 0.961 with all loads of a line before its stores; degree 7: 0.280 vs 0.230).
+// The neighbour traces through the read-only path, with or without an L1 evict_last hint,
+// measured the same as plain loads (0.922-0.924 ms).
 // Phase profile at 64^3 (clock64 at one thread per CTA, all four RK4 stages, cycles per tile of
 // four elements): copy wait 3.1k, axis 0 2.2k, axis 1 3.1k, axis 2 3.4k, update 4.1k; with four
 // CTAs per SM in these phases the SM issues about half of the cycles.
